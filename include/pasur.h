@@ -1,0 +1,175 @@
+/*
+ * pasur.h -- C ABI of the GB300 (sm_103a) exact round-by-round CFR solver for two-player,
+ * open-hand, fixed-deck Pasur, after "Solving Pasur Using GPU-Accelerated Counterfactual Regret
+ * Minimization" (arXiv 2508.06559).
+ *
+ * General rules for every entry point
+ *   - Every call returns a pasur_status (0 = PASUR_OK, negative = error).  No C++ exception
+ *     crosses this boundary.  After an error, pasur_last_error(ctx) holds a one-line message.
+ *   - Pointers documented as "host or device" may point to host memory or to device memory of
+ *     the context's device; the library detects which.  Device pointers are used on the
+ *     context's stream; host results are complete when the call returns.
+ *   - Caller-owned buffers are never retained after a call returns.
+ *   - Outputs follow query-then-fill: pass NULL (or cap = 0) to learn the required size.
+ *   - Objects returned through an out-parameter (pasur_ctx, pasur_tree) are owned by the caller
+ *     and released with pasur_destroy / pasur_tree_free.  A tree must be freed before its ctx.
+ *   - Cards are ids 0..51, id = 4*rank + suit, rank 0 = Ace .. 9 = Ten, 10 = Jack, 11 = Queen,
+ *     12 = King; suit 0 = clubs, 1 = diamonds, 2 = hearts, 3 = spades (the paper's Fig.
+ *     "Mapping Cards to Indices").  A card set is a uint64_t with bit id set.
+ *   - Player 0 (Alex) moves first in every round; utilities are Alex's points minus Bob's.
+ */
+#ifndef PASUR_H
+#define PASUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pasur_ctx pasur_ctx;   /* one device + one stream + a device-memory budget */
+typedef struct pasur_tree pasur_tree; /* one round: game tree, full game tree, CFR state  */
+
+typedef enum {
+    PASUR_OK = 0,
+    PASUR_EINVAL = -1,    /* bad argument (sizes, round index, unsorted roots, wrong phase)  */
+    PASUR_ENOMEM = -2,    /* device allocation failed or would exceed the ctx budget          */
+    PASUR_EOVERFLOW = -3, /* a size does not fit its index type or a caller buffer (cap)      */
+    PASUR_ECUDA = -4,     /* a CUDA runtime call failed; the message names it                 */
+    PASUR_ETIMEOUT = -5,  /* a bounded device wait gave up                                     */
+    PASUR_ENUMERIC = -6,  /* a non-finite value appeared in the CFR sweep                      */
+    PASUR_ENOTIMPL = -7
+} pasur_status;
+
+/* Score inherited from earlier rounds: one row of the paper's score tensor t_scr (Table
+ * "Column definitions for the score tensor"): Alex clubs, Bob clubs, point difference
+ * (Alex minus Bob), 7-clubs bonus (0 none, 1 Alex, 2 Bob).  Normalised: once a bonus is
+ * recorded both club counts are 0 (section "Score Tensors"). */
+typedef struct {
+    int16_t a_clubs, b_clubs, delta, bonus;
+} pasur_score;
+
+/* Solver settings.
+ *   variant      0 = vanilla CFR (eq. RM + eq. avsigma), 1 = DCFR (eqs. DFCR_REG / DFCR_AVG)
+ *   iters        number of iterations run by one pasur_cfr_iterate call (>= 0)
+ *   rm_deadzone  tau: a cumulative regret counts as positive only above tau * t * Umax,
+ *                Umax = max |leaf value| of the round, t = iteration index (1-based)
+ *   dcfr_alpha/beta/gamma  DCFR discount exponents (the paper ran 1.5, 0, 2)
+ *   slots_per_item  score slots solved together by one thread block (0 = choose automatically)
+ *   threads      threads per block of the CFR kernel (0 = choose automatically)
+ */
+typedef struct {
+    int32_t variant;
+    int32_t iters;
+    float rm_deadzone;
+    float dcfr_alpha, dcfr_beta, dcfr_gamma;
+    int32_t slots_per_item;
+    int32_t threads;
+} pasur_config;
+
+/* Fill *cfg with the defaults: vanilla, 1000 iterations, tau = 1e-6, DCFR (1.5, 0, 2). */
+int pasur_config_default(pasur_config *cfg);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no limit beyond the
+ * device's memory.  cuda_stream is a cudaStream_t (NULL = a new non-blocking stream owned by
+ * the context). */
+int pasur_create(pasur_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+/* Release the context.  EINVAL (and nothing is released) while trees of the context are alive. */
+int pasur_destroy(pasur_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of the last failed pasur_create when ctx is NULL).
+ * The string is owned by the library and valid until the next call on ctx. */
+const char *pasur_last_error(const pasur_ctx *ctx);
+
+/* Bytes of device memory the context holds now and at its peak. */
+int pasur_memory(const pasur_ctx *ctx, size_t *in_use, size_t *peak);
+
+/* Number of CUDA kernels launched through ctx since its creation (host out). */
+int pasur_launch_count(const pasur_ctx *ctx, int64_t *count);
+
+/* Seeded deal (section "Pasur", initial pool rule): SplitMix64-seeded xoshiro256**,
+ * unbiased Fisher-Yates over 0..51 (i = 51..1, j uniform in [0, i]); deck[0:4] is the initial
+ * pool and holds no Jack: one Jack is swapped with deck[4] unless deck[4] is a Jack too, and two
+ * or more Jacks force a fresh shuffle of 0..51 with the stream continued.  Round r (0..5) deals
+ * deck[4+8r : 8+8r] to Alex and deck[8+8r : 12+8r] to Bob.  Host only; deck_out is host memory. */
+int pasur_deal(uint64_t seed, uint8_t deck_out[52]);
+
+/* Build the level-ordered game tree (GT) of round `round` (0..5; 5 = final) for the given root
+ * pools (section "Actions", CodeSnippet "ApplyActions", Table "Capture rules for each card type").
+ * root_pools (host or device): n_pools card sets, strictly ascending, disjoint from the round's
+ * hands.  Level 0 holds the roots; level k+1 holds the children of level k's nodes in parent
+ * order, each node's children sorted by (played card, picked set as an integer).  Legal moves:
+ * a numeric card takes any nonempty set of pool numerics completing its value to 11 (one move per
+ * set) or, with none, is laid; a Jack takes every pool card that is not a King or Queen (laid if
+ * there is none); a Queen or King takes one pool card of its rank (one move each) or is laid.
+ * Errors: EINVAL (round, unsorted/overlapping pools), ENOMEM, EOVERFLOW. */
+int pasur_build_round(pasur_ctx *ctx, const uint8_t deck[52], int round, const uint64_t *root_pools,
+                      int64_t n_pools, pasur_tree **out);
+int pasur_tree_free(pasur_tree *tree);
+
+/* GT level sizes and, once unfolded, full-game-tree (FGT) level sizes (-1 before).  Host out. */
+int pasur_tree_sizes(const pasur_tree *tree, int64_t gt_sizes[9], int64_t fgt_sizes[9]);
+
+/* Unfolding Process (section "In-Hand Updates", Fig. "Unfolding Process"): GT root g carries the
+ * score slots score_offs[g] .. score_offs[g+1]-1 of `scores`; every FGT level lists, for each GT
+ * node of the level in order, one node per slot of its root (GT-major, slot-minor), so FGT node
+ * (j, s) has parent (parent(j), s).  score_offs: n_pools+1 int64 (host), scores: host array.
+ * Scores of one root must be strictly ascending in (a_clubs, b_clubs, delta, bonus) order.
+ * level_sizes_out (host, may be NULL) receives the 9 FGT level sizes.  Resets any CFR state. */
+int pasur_unfold(pasur_tree *tree, const int64_t *score_offs, const pasur_score *scores,
+                 int64_t level_sizes_out[9]);
+
+/* Run cfg->iters iterations of CFR on an unfolded round (section "CFR Algorithm"): each FGT node
+ * is its own information set; root reach 1 for both players; per iteration regret matching
+ * (eq. RM, with the cfg dead zone), reach top-down, values bottom-up, then R(h,a) +=
+ * s_p pi_{-p}(h) (v(h.a) - v(h)) and S(h,a) += pi_p(h) sigma(h,a) (eq. avsigma) for every edge,
+ * and the root value is accumulated.  The first call after pasur_unfold fixes the leaf values:
+ * final round: this round's point difference after CleanUp plus +7 / -7 for the 7-clubs bonus
+ * (eq. final_util); other rounds: the round's point difference plus next_root_util[lnk(leaf)]
+ * (eq. passuputil), with the links of pasur_next_roots (which must have been called).
+ * next_root_util: float per next-round FGT root, host or device; NULL for the final round; it is
+ * read only on the first call.  Later calls continue the same run.  Errors: EINVAL, ENUMERIC. */
+int pasur_cfr_iterate(pasur_tree *tree, const pasur_config *cfg, const float *next_root_util);
+
+/* Average strategy (eq. avsigma, normalised per FGT parent; uniform where the strategy sum is 0)
+ * of every FGT edge: levels 1..8 concatenated, each level in FGT order.  out: float, host or
+ * device, cap = its length in elements (>= sum of FGT level sizes 1..8, else EOVERFLOW). */
+int pasur_avg_strategy(const pasur_tree *tree, float *out, int64_t cap);
+
+/* Average root utility of every FGT root (sum over iterations of v(root), divided by the number
+ * of iterations; CodeSnippet "CFR").  out: float, host or device, cap >= FGT level-0 size. */
+int pasur_round_utilities(const pasur_tree *tree, float *out, int64_t cap);
+
+/* Between-hand update (section "Between-Hand Updates", CodeSnippet "BetweenHands"): the next
+ * round's FGT roots.  For every FGT leaf (j, s) the next root is (pool at j, normalise(score s +
+ * the round's clubs and point difference at j)).  Roots: unique pools ascending, per pool unique
+ * scores ascending.  Outputs (host; any may be NULL to query): pools_out[n_pools],
+ * score_offs_out[n_pools+1], scores_out[n_roots], lnk_out[FGT leaves] (index of each leaf's next
+ * root, the paper's t_lnk).  The links are also kept on the device for pasur_cfr_iterate.
+ * cap_pools / cap_roots bound the two arrays; too small -> EOVERFLOW with the sizes still set.
+ * Not valid for the final round (EINVAL). */
+int pasur_next_roots(pasur_tree *tree, uint64_t *pools_out, int64_t cap_pools, int64_t *score_offs_out,
+                     pasur_score *scores_out, int64_t cap_roots, int64_t *lnk_out, int64_t *n_pools,
+                     int64_t *n_roots);
+
+/* Export GT level k (0..8) for parity checks; every output is host memory and may be NULL:
+ * parent[n] (int64, level k-1 index; -1 at level 0), nchild[n] (int32; 0 at level 8),
+ * lay[n] (int32 card played into the node; -1 at level 0), pick[n] (uint64 picked set),
+ * state[3n] (Alex hand, Bob hand, pool), rus[7n] (int8 running score: Alex clubs, Bob clubs,
+ * last picker 0/1/2, Alex points, Alex surs, Bob points, Bob surs).  cap = n of the caller. */
+int pasur_export_level(const pasur_tree *tree, int k, int64_t cap, int64_t *parent, int32_t *nchild,
+                       int32_t *lay, uint64_t *pick, uint64_t *state, int8_t *rus);
+
+/* Export the FGT leaf values fixed by the first pasur_cfr_iterate call (float per FGT leaf,
+ * host or device).  EINVAL before that call. */
+int pasur_leaf_values(const pasur_tree *tree, float *out, int64_t cap);
+
+/* Timing of the last pasur_cfr_iterate call on the device (CUDA events around the CFR kernel
+ * launches), the number of FGT edges, and the kernel launches it made. */
+int pasur_last_cfr_stats(const pasur_tree *tree, float *ms, int64_t *edges, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASUR_H */

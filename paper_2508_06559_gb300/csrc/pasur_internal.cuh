@@ -1,0 +1,233 @@
+// Internal declarations of the Pasur GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pasur.h"
+
+// ---------------------------------------------------------------------------------------------
+// Cards (the paper's Fig. "Mapping Cards to Indices" and Table card index sets):
+// id = 4*rank + suit; ranks Ace..Ten are the numeric cards 0..39, Jacks 40..43, Queens 44..47,
+// Kings 48..51; clubs are the ids divisible by 4.
+// ---------------------------------------------------------------------------------------------
+namespace pasur {
+
+constexpr uint64_t kNumeric = (1ULL << 40) - 1ULL;
+constexpr uint64_t kJacks = 0xFULL << 40;
+constexpr uint64_t kQueens = 0xFULL << 44;
+constexpr uint64_t kKings = 0xFULL << 48;
+constexpr uint64_t kClubs = 0x0001111111111111ULL;  // bits 0, 4, ..., 48
+constexpr uint64_t kAces = 0xFULL;
+constexpr int kTwoClubs = 4;
+constexpr int kTenDiamonds = 37;
+
+// Points of a captured set (Table "Pasur Scoring System"): Aces and Jacks 1, two of clubs 2,
+// ten of diamonds 3.
+__host__ __device__ __forceinline__ int set_points(uint64_t m) {
+#ifdef __CUDA_ARCH__
+    return __popcll(m & (kAces | kJacks)) + 2 * (int)((m >> kTwoClubs) & 1ULL) +
+           3 * (int)((m >> kTenDiamonds) & 1ULL);
+#else
+    return __builtin_popcountll(m & (kAces | kJacks)) + 2 * (int)((m >> kTwoClubs) & 1ULL) +
+           3 * (int)((m >> kTenDiamonds) & 1ULL);
+#endif
+}
+
+__host__ __device__ __forceinline__ int set_clubs(uint64_t m) {
+#ifdef __CUDA_ARCH__
+    return __popcll(m & kClubs);
+#else
+    return __builtin_popcountll(m & kClubs);
+#endif
+}
+
+// Running score of a round packed in bytes of a uint64 (Table "Column definitions for the
+// running-score tensor"): [0] Alex clubs [1] Bob clubs [2] last picker (0/1/2) [3] Alex points
+// [4] Alex surs [5] Bob points [6] Bob surs.
+__host__ __device__ __forceinline__ int rus_get(uint64_t r, int f) { return (int)((r >> (8 * f)) & 0xFFULL); }
+__host__ __device__ __forceinline__ uint64_t rus_add(uint64_t r, int f, int v) { return r + ((uint64_t)(uint32_t)v << (8 * f)); }
+__host__ __device__ __forceinline__ uint64_t rus_set(uint64_t r, int f, int v) {
+    return (r & ~(0xFFULL << (8 * f))) | ((uint64_t)(v & 0xFF) << (8 * f));
+}
+// Alex minus Bob points of the round, 5 per Sur.
+__host__ __device__ __forceinline__ int rus_diff(uint64_t r) {
+    return (rus_get(r, 3) + 5 * rus_get(r, 4)) - (rus_get(r, 5) + 5 * rus_get(r, 6));
+}
+
+struct __align__(16) GTState {
+    uint64_t hand[2];  // Alex, Bob
+    uint64_t pool;
+    uint64_t rus;
+};
+
+// Score normalisation (section "Score Tensors"): a player with at least 7 clubs earns the bonus and
+// both club counts reset to 0; with a bonus recorded clubs are not tracked.
+__host__ __device__ __forceinline__ void normalize_score(int &ac, int &bc, int &bonus) {
+    if (bonus == 0) {
+        if (ac >= 7) { ac = 0; bc = 0; bonus = 1; }
+        else if (bc >= 7) { ac = 0; bc = 0; bonus = 2; }
+    } else {
+        ac = 0;
+        bc = 0;
+    }
+}
+
+// Sort key of a score: ascending key = lexicographic (a_clubs, b_clubs, delta, bonus), signed.
+__host__ __device__ __forceinline__ uint32_t score_key(int ac, int bc, int delta, int bonus) {
+    return ((uint32_t)ac << 22) | ((uint32_t)bc << 18) | ((uint32_t)(delta + 32768) << 2) | (uint32_t)bonus;
+}
+__host__ __device__ __forceinline__ void score_unkey(uint32_t k, int &ac, int &bc, int &delta, int &bonus) {
+    ac = (int)(k >> 22);
+    bc = (int)((k >> 18) & 0xF);
+    delta = (int)((k >> 2) & 0xFFFF) - 32768;
+    bonus = (int)(k & 3);
+}
+constexpr int kScoreKeyBits = 26;
+
+}  // namespace pasur
+
+// ---------------------------------------------------------------------------------------------
+// Context and tree objects
+// ---------------------------------------------------------------------------------------------
+struct pasur_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, in_use = 0, peak = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    // capture table of numeric moves: per numeric card c, the picked sets completing it to 11,
+    // ascending; tab_off[41]
+    uint64_t *tab = nullptr;
+    int32_t *tab_off = nullptr;
+    int32_t *counter = nullptr;  // work-queue counters (device)
+    int32_t *errflag = nullptr;  // device error word
+    int64_t launches = 0;        // kernels launched through this context
+    int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
+};
+
+struct RootInfo {             // one GT root's subtree, level by level
+    int64_t lvl_begin[9];     // first GT node of the root at level k
+    int32_t lvl_count[9];     // its GT nodes at level k
+    int32_t local_start[10];  // local (level-major) index of its first node at level k; [9] = nodes
+    int64_t struct_off;       // offset of its internal nodes in the local structure arrays
+    int32_t n_internal;       // nodes at levels 0..7
+    int32_t pad;
+};
+
+struct CfrItem {              // one work item of the CFR kernel: a root and a run of its slots
+    int32_t root;
+    int32_t ns;               // slots in the item
+    int64_t s0;               // first slot of the item within its root
+    int64_t data_base;        // offset of the item's (local node, slot) table in R and S
+    int64_t scratch_base;     // offset in the global transients, or -1 when the item is resident
+    int64_t cost;             // nodes * slots, for the schedule
+};
+
+struct pasur_tree {
+    pasur_ctx *ctx = nullptr;
+    int round = 0;
+    bool final_round = false;
+    uint8_t deck[52];
+    uint64_t hand_a = 0, hand_b = 0;
+    int64_t n_roots = 0;
+    int64_t M[9] = {0};
+    // game tree, level by level (device)
+    pasur::GTState *st[9] = {nullptr};
+    int64_t *child_off[9] = {nullptr};  // levels 0..7: M[k]+1
+    int64_t *parent[9] = {nullptr};     // levels 1..8
+    int8_t *lay[9] = {nullptr};         // levels 1..8
+    uint64_t *pick[9] = {nullptr};      // levels 1..8
+    int32_t *root[9] = {nullptr};       // root id of every node
+    std::vector<RootInfo> roots_h;
+    RootInfo *roots_d = nullptr;
+    // full game tree
+    bool unfolded = false;
+    int64_t Q[9] = {0};
+    int64_t *fgt_off[9] = {nullptr};    // M[k]+1
+    int64_t *score_off_d = nullptr;
+    pasur_score *scores_d = nullptr;
+    std::vector<int64_t> score_off_h;
+    // next round links
+    bool has_next = false;
+    int64_t *lnk_d = nullptr;           // Q[8]
+    int64_t n_next_roots = 0;
+    std::vector<uint64_t> next_pools_h;
+    std::vector<int64_t> next_soff_h;
+    std::vector<pasur_score> next_scores_h;
+    // CFR state
+    bool cfr_ready = false;
+    int64_t iters_done = 0;
+    float umax = 0.f;
+    float *leaf_v = nullptr;            // Q[8], FGT order
+    int32_t *lcs = nullptr;             // local first child of every internal node
+    uint16_t *ldeg = nullptr;           // its number of children
+    std::vector<CfrItem> items_h;
+    CfrItem *items_d = nullptr;
+    int64_t n_items = 0, data_size = 0, scratch_size = 0;
+    float *R = nullptr, *S = nullptr;   // per (local node, slot) of every item
+    float *V = nullptr, *P0 = nullptr, *P1 = nullptr;  // transients of the non-resident items
+    double *uacc = nullptr;             // Q[0]
+    int cfr_threads = 0, cfr_blocks = 0;
+    size_t cfr_smem = 0;
+    int32_t variant = -1;
+    float last_ms = 0.f;
+    int32_t last_launches = 0;
+    std::vector<void *> allocs;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Helpers shared by the library's translation units
+// ---------------------------------------------------------------------------------------------
+namespace pasur {
+
+int set_err(pasur_ctx *ctx, int code, const std::string &msg);
+int cuda_err(pasur_ctx *ctx, cudaError_t e, const char *what);
+int dev_alloc(pasur_ctx *ctx, void **p, size_t bytes);
+void dev_free(pasur_ctx *ctx, void *p, size_t bytes);
+int tree_alloc(pasur_tree *t, void **p, size_t bytes);  // freed with the tree
+bool is_device_ptr(const void *p);
+
+#define PASUR_CUDA(ctx, call)                                   \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::pasur::cuda_err((ctx), e_, #call); \
+    } while (0)
+#define PASUR_TRY(call)            \
+    do {                           \
+        int rc_ = (call);          \
+        if (rc_ != PASUR_OK) return rc_; \
+    } while (0)
+
+// scan_sort.cu
+// out[i] = sum_{j<i} in[i] for i in [0, n], out has n+1 entries (out[n] = total); in is int32
+// or int64 (device).  Scratch is allocated from ctx.
+int exclusive_scan_i32(pasur_ctx *ctx, const int32_t *in, int64_t *out, int64_t n);
+int exclusive_scan_i64(pasur_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
+// stable LSD radix sort of (key, value) pairs by the low `bits` bits of key (device, in place
+// through ping-pong buffers allocated inside)
+int radix_sort_pairs(pasur_ctx *ctx, uint64_t *keys, int64_t *vals, int64_t n, int bits);
+int read_i64(pasur_ctx *ctx, const int64_t *dptr, int64_t *out);
+
+// build.cu
+int ensure_capture_table(pasur_ctx *ctx);
+int build_levels(pasur_tree *t, const uint64_t *root_pools_dev);
+int unfold_levels(pasur_tree *t);
+int compute_leaf_values(pasur_tree *t, const float *next_util_dev);
+
+// cfr.cu
+int cfr_prepare(pasur_tree *t, const pasur_config *cfg);
+int cfr_run(pasur_tree *t, const pasur_config *cfg);
+int cfr_export_sigma(const pasur_tree *t, float *out_dev);
+int cfr_export_utilities(const pasur_tree *t, float *out_dev);
+
+// between.cu
+int next_roots(pasur_tree *t, std::vector<uint64_t> &pools, std::vector<int64_t> &score_off,
+               std::vector<pasur_score> &scores);
+
+}  // namespace pasur

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of the Pasur GB300 C ABI (include/pasur.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libpasur.so``.  There is no CPU fallback: if the library is missing or no CUDA device is
+present, the calls raise.  Arrays may be numpy arrays (host) or torch CUDA tensors (device); the
+library detects which.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpasur.so")
+
+PASUR_OK, PASUR_EINVAL, PASUR_ENOMEM, PASUR_EOVERFLOW = 0, -1, -2, -3
+PASUR_ECUDA, PASUR_ETIMEOUT, PASUR_ENUMERIC, PASUR_ENOTIMPL = -4, -5, -6, -7
+_NAMES = {0: "PASUR_OK", -1: "PASUR_EINVAL", -2: "PASUR_ENOMEM", -3: "PASUR_EOVERFLOW", -4: "PASUR_ECUDA",
+          -5: "PASUR_ETIMEOUT", -6: "PASUR_ENUMERIC", -7: "PASUR_ENOTIMPL"}
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTS = [
+    "pasur_config_default", "pasur_create", "pasur_destroy", "pasur_last_error", "pasur_memory", "pasur_launch_count",
+    "pasur_deal",
+    "pasur_build_round", "pasur_tree_free", "pasur_tree_sizes", "pasur_unfold", "pasur_cfr_iterate",
+    "pasur_avg_strategy", "pasur_round_utilities", "pasur_next_roots", "pasur_export_level", "pasur_leaf_values",
+    "pasur_last_cfr_stats",
+]
+
+
+class PasurError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pasur_score(C.Structure):
+    _fields_ = [("a_clubs", C.c_int16), ("b_clubs", C.c_int16), ("delta", C.c_int16), ("bonus", C.c_int16)]
+
+
+class pasur_config(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("iters", C.c_int32), ("rm_deadzone", C.c_float), ("dcfr_alpha", C.c_float),
+                ("dcfr_beta", C.c_float), ("dcfr_gamma", C.c_float), ("slots_per_item", C.c_int32),
+                ("threads", C.c_int32)]
+
+
+_lib = None
+vp = C.c_void_p
+i64 = C.c_int64
+i64p = C.POINTER(C.c_int64)
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"Pasur CUDA library not built ({LIB_PATH}); run paper_2508_06559_gb300/build.py")
+    L = C.CDLL(LIB_PATH)
+    L.pasur_config_default.argtypes = [C.POINTER(pasur_config)]
+    L.pasur_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t, vp]
+    L.pasur_destroy.argtypes = [vp]
+    L.pasur_last_error.argtypes = [vp]
+    L.pasur_last_error.restype = C.c_char_p
+    L.pasur_memory.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    L.pasur_launch_count.argtypes = [vp, i64p]
+    L.pasur_deal.argtypes = [C.c_uint64, vp]
+    L.pasur_build_round.argtypes = [vp, vp, C.c_int, vp, i64, C.POINTER(vp)]
+    L.pasur_tree_free.argtypes = [vp]
+    L.pasur_tree_sizes.argtypes = [vp, vp, vp]
+    L.pasur_unfold.argtypes = [vp, vp, vp, vp]
+    L.pasur_cfr_iterate.argtypes = [vp, C.POINTER(pasur_config), vp]
+    L.pasur_avg_strategy.argtypes = [vp, vp, i64]
+    L.pasur_round_utilities.argtypes = [vp, vp, i64]
+    L.pasur_next_roots.argtypes = [vp, vp, i64, vp, vp, i64, vp, i64p, i64p]
+    L.pasur_export_level.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, vp, vp]
+    L.pasur_leaf_values.argtypes = [vp, vp, i64]
+    L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
+    for name in EXPORTS:
+        if name != "pasur_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(rc: int, ctx_handle=None):
+    if rc != PASUR_OK:
+        msg = load().pasur_last_error(ctx_handle)
+        raise PasurError(rc, msg.decode() if msg else "")
+
+
+def pasur_config_default(**over) -> pasur_config:
+    cfg = pasur_config()
+    _check(load().pasur_config_default(C.byref(cfg)))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def pasur_deal(seed: int) -> np.ndarray:
+    deck = np.zeros(52, np.uint8)
+    _check(load().pasur_deal(C.c_uint64(seed), _ptr(deck)))
+    return deck
+
+
+def scores_array(rows) -> np.ndarray:
+    """(n,4) int16 rows (a_clubs, b_clubs, delta, bonus) -> contiguous pasur_score array."""
+    return np.ascontiguousarray(np.asarray(rows, np.int16).reshape(-1, 4))
+
+
+class Ctx:
+    """pasur_create / pasur_destroy."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+        h = vp()
+        rc = load().pasur_create(C.byref(h), device, hbm_budget_bytes, stream)
+        _check(rc, None)
+        self.h = h
+        self._trees = weakref.WeakSet()
+
+    def close(self):
+        """Free the context's remaining trees, then the context."""
+        if self.h:
+            for t in list(self._trees):
+                t.free()
+            _check(load().pasur_destroy(self.h), self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory(self):
+        a, b = C.c_size_t(0), C.c_size_t(0)
+        _check(load().pasur_memory(self.h, C.byref(a), C.byref(b)), self.h)
+        return a.value, b.value
+
+    def pasur_launch_count(self) -> int:
+        n = C.c_int64(0)
+        _check(load().pasur_launch_count(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def pasur_build_round(self, deck, rnd: int, root_pools) -> "Tree":
+        d = np.ascontiguousarray(deck, np.uint8)
+        pools = root_pools if hasattr(root_pools, "data_ptr") else np.ascontiguousarray(root_pools, np.uint64)
+        n = pools.numel() if hasattr(pools, "numel") else len(pools)
+        th = vp()
+        _check(load().pasur_build_round(self.h, _ptr(d), rnd, _ptr(pools), n, C.byref(th)), self.h)
+        t = Tree(self, th)
+        self._trees.add(t)
+        return t
+
+
+class Tree:
+    """One round: wraps the pasur_tree calls (names as in the C ABI)."""
+
+    def __init__(self, ctx: Ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def free(self):
+        if self.h and self.ctx.h:
+            load().pasur_tree_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self.ctx.h)
+
+    def pasur_tree_sizes(self):
+        g = np.zeros(9, np.int64)
+        q = np.zeros(9, np.int64)
+        self._c(load().pasur_tree_sizes(self.h, _ptr(g), _ptr(q)))
+        return g, q
+
+    def pasur_unfold(self, score_offs, scores) -> np.ndarray:
+        so = np.ascontiguousarray(score_offs, np.int64)
+        sc = scores_array(scores)
+        q = np.zeros(9, np.int64)
+        self._c(load().pasur_unfold(self.h, _ptr(so), _ptr(sc), _ptr(q)))
+        return q
+
+    def unfold_single(self, score=(0, 0, 0, 0)) -> np.ndarray:
+        r = int(self.pasur_tree_sizes()[0][0])
+        return self.pasur_unfold(np.arange(r + 1, dtype=np.int64), np.tile(np.asarray(score, np.int16), (r, 1)))
+
+    def pasur_cfr_iterate(self, cfg: pasur_config, next_root_util=None):
+        nu = None
+        if next_root_util is not None:
+            nu = next_root_util if hasattr(next_root_util, "data_ptr") else np.ascontiguousarray(next_root_util, np.float32)
+        self._c(load().pasur_cfr_iterate(self.h, C.byref(cfg), _ptr(nu)))
+
+    def n_edges(self) -> int:
+        return int(self.pasur_tree_sizes()[1][1:].sum())
+
+    def pasur_avg_strategy(self, out=None):
+        ne = self.n_edges()
+        if out is None:
+            out = np.zeros(ne, np.float32)
+        n = out.numel() if hasattr(out, "numel") else len(out)
+        self._c(load().pasur_avg_strategy(self.h, _ptr(out), n))
+        return out
+
+    def pasur_round_utilities(self, out=None):
+        q0 = int(self.pasur_tree_sizes()[1][0])
+        if out is None:
+            out = np.zeros(q0, np.float32)
+        n = out.numel() if hasattr(out, "numel") else len(out)
+        self._c(load().pasur_round_utilities(self.h, _ptr(out), n))
+        return out
+
+    def pasur_next_roots(self):
+        npool, nroot = C.c_int64(0), C.c_int64(0)
+        self._c(load().pasur_next_roots(self.h, None, 0, None, None, 0, None, C.byref(npool), C.byref(nroot)))
+        pools = np.zeros(npool.value, np.uint64)
+        soff = np.zeros(npool.value + 1, np.int64)
+        scores = np.zeros((nroot.value, 4), np.int16)
+        lnk = np.zeros(int(self.pasur_tree_sizes()[1][8]), np.int64)
+        self._c(load().pasur_next_roots(self.h, _ptr(pools), npool.value, _ptr(soff), _ptr(scores), nroot.value,
+                                        _ptr(lnk), C.byref(npool), C.byref(nroot)))
+        return pools, soff, scores, lnk
+
+    def pasur_next_roots_nolinks(self):
+        """Next roots without copying the links to the host (they stay on the device)."""
+        npool, nroot = C.c_int64(0), C.c_int64(0)
+        self._c(load().pasur_next_roots(self.h, None, 0, None, None, 0, None, C.byref(npool), C.byref(nroot)))
+        pools = np.zeros(npool.value, np.uint64)
+        soff = np.zeros(npool.value + 1, np.int64)
+        scores = np.zeros((nroot.value, 4), np.int16)
+        self._c(load().pasur_next_roots(self.h, _ptr(pools), npool.value, _ptr(soff), _ptr(scores), nroot.value,
+                                        None, C.byref(npool), C.byref(nroot)))
+        return pools, soff, scores, None
+
+    def pasur_export_level(self, k: int):
+        n = int(self.pasur_tree_sizes()[0][k])
+        parent = np.zeros(n, np.int64)
+        nchild = np.zeros(n, np.int32)
+        lay = np.zeros(n, np.int32)
+        pick = np.zeros(n, np.uint64)
+        state = np.zeros((n, 3), np.uint64)
+        rus = np.zeros((n, 7), np.int8)
+        self._c(load().pasur_export_level(self.h, k, n, _ptr(parent), _ptr(nchild), _ptr(lay), _ptr(pick),
+                                          _ptr(state), _ptr(rus)))
+        return dict(parent=parent, nchild=nchild, lay=lay, pick=pick, state=state, rus=rus)
+
+    def pasur_leaf_values(self, out=None):
+        q8 = int(self.pasur_tree_sizes()[1][8])
+        if out is None:
+            out = np.zeros(q8, np.float32)
+        n = out.numel() if hasattr(out, "numel") else len(out)
+        self._c(load().pasur_leaf_values(self.h, _ptr(out), n))
+        return out
+
+    def pasur_last_cfr_stats(self):
+        ms, e, l = C.c_float(0), C.c_int64(0), C.c_int32(0)
+        self._c(load().pasur_last_cfr_stats(self.h, C.byref(ms), C.byref(e), C.byref(l)))
+        return ms.value, e.value, l.value
