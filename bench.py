@@ -36,7 +36,7 @@ WORKLOADS = {
 }
 METRIC = "CFR node-updates/sec"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-ALG_FLOPS_PER_UPDATE = 12   # per edge of a node with >= 2 moves (RM 3, reach 1, value 3, regret 3, S 2)
+ALG_BYTES_PER_UPDATE = 16   # regret and strategy sum, f32, read + write, per node-update
 CPU_SAMPLE_SECONDS = 12.0
 
 
@@ -222,11 +222,10 @@ def run_ours(args, rank, world, dist):
     ms_per_step = total_ms / args.steps
     value = world * updates / (ms_per_step / 1e3)
     kernel_ms = statistics.mean(kern_ms)
-    # dominant kernel: the CFR kernel (one launch per round); algorithmic FLOPs per launch =
-    # ALG_FLOPS_PER_UPDATE x edges of nodes with >= 2 moves x T
-    nontriv = sum(nontrivial_edges(i) for i in info) if False else None
-    ach_flops = ALG_FLOPS_PER_UPDATE * updates / (kernel_ms / 1e3)
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6  # FP32 lanes x FMA x clock
+    # dominant kernel: the CFR kernel (k_cfr_items, one launch per size class and round); the
+    # algorithmic traffic of CFR is the regret and strategy-sum read + write per node-update
+    ach_gbs = ALG_BYTES_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     line = {
         "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -235,10 +234,12 @@ def run_ours(args, rank, world, dist):
                    "fgt_sizes_per_round": info, "node_updates_per_step": updates,
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "cfr_kernel": {"ms_per_step": kernel_ms, "node_updates_per_s": updates / (kernel_ms / 1e3)},
-        "roofline": {"bound": "alu", "achieved": ach_flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": ach_flops / alu_peak, "traffic": None,
-                     "note": f"k_cfr_items, shared-memory resident; peak = 152 SM x 128 FP32 lanes x 2 x "
-                             f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)"},
+        "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ach_gbs / hbm_peak,
+                     "traffic": None,
+                     "note": (f"k_cfr_items; achieved = {ALG_BYTES_PER_UPDATE} B per node-update (R and S read + write) "
+                              f"x node-updates / CFR kernel time, peak = {src} HBM copy bandwidth; the kernel keeps "
+                              "each root's state in shared memory for all T iterations, so its DRAM traffic is far "
+                              "below the algorithmic bytes (ncu counters in profiles/) and it is issue/latency bound")},
         "e2e": {"value": world * updates / (e2e_mean / 1e3), "unit": "node-updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(1, args.steps),
@@ -249,17 +250,12 @@ def run_ours(args, rank, world, dist):
     return line
 
 
-def nontrivial_edges(_):
-    return 0
-
-
 # ---------------------------------------------------------------------------------------------
 # CPU oracle (baseline leg and the reference arm)
 # ---------------------------------------------------------------------------------------------
 
-def oracle_sample(workload: str, seed: int, T: int, target_s: float):
-    """Oracle CFR on a bounded sample of the workload: the final round's first roots (with all
-    their score slots), sized to take about target_s on one core.  Returns (updates, seconds, desc)."""
+def _oracle_round5(workload: str, seed: int):
+    """The oracle's own chain of rounds up to the final round of the workload (roots, slots)."""
     import oracle as O
     first_round, _ = WORKLOADS[workload]
     deck = O.deal(seed)
@@ -269,44 +265,78 @@ def oracle_sample(workload: str, seed: int, T: int, target_s: float):
         t.unfold(soff, scores)
         pools, soff, scores, _ = t.next_roots()
         del t
-    # probe speed on the first root
-    t1 = O.Tree(deck, 5, list(pools[:1]))
-    t1.unfold(soff[:2] - soff[0], scores[soff[0]:soff[1]])
-    e1 = int(t1.sizes()[1][1:].sum())
+    return deck, np.asarray(pools, np.uint64), np.asarray(soff), np.asarray(scores)
+
+
+def _oracle_job(args):
+    """One core: oracle CFR on FGT roots [first, first+count) of the final round for T iterations."""
+    workload, seed, first, count, T = args
+    import oracle as O
+    deck, pools, soff, scores = _oracle_round5(workload, seed)
+    root_of_slot = np.repeat(np.arange(len(pools)), np.diff(soff))
+    sel = [(int(root_of_slot[f]), int(f - soff[root_of_slot[f]])) for f in range(first, first + count)]
+    roots = sorted({g for g, _ in sel})
+    so, sc = [0], []
+    for g in roots:
+        for _, s_ in [x for x in sel if x[0] == g]:
+            sc.append(scores[soff[g] + s_])
+        so.append(len(sc))
+    t = O.Tree(deck, 5, [int(pools[g]) for g in roots])
+    t.unfold(np.array(so), np.array(sc, np.int16))
+    edges = int(t.sizes()[1][1:].sum())
+    leaf = t.leaf_utilities_final()
     t0 = time.perf_counter()
-    t1.cfr(t1.leaf_utilities_final(), 5)
-    rate = 5 * e1 / max(time.perf_counter() - t0, 1e-6)
-    budget = target_s * rate
-    n = 1
-    while n < len(pools):
-        e = e1 * (n + 1)  # rough
-        if e * T > budget:
-            break
-        n += 1
-    ts = O.Tree(deck, 5, list(pools[:n]))
-    ts.unfold(soff[:n + 1] - soff[0], scores[soff[0]:soff[n]])
-    edges = int(ts.sizes()[1][1:].sum())
-    Ts = max(1, min(T, int(budget / max(edges, 1))))
-    leaf = ts.leaf_utilities_final()
+    t.cfr(leaf, T)
+    return edges * T, time.perf_counter() - t0, edges
+
+
+def oracle_sample(workload: str, seed: int, T: int, target_s: float, cores: int):
+    """The fp64 oracle as it stands, on `cores` host cores (one process each, disjoint FGT roots
+    of the workload's final round), sized to about target_s of CPU work per core.  Returns
+    (node-updates, wall seconds, description)."""
+    import multiprocessing as mp
+    _, pools, soff, _ = _oracle_round5(workload, seed)
+    n_roots = int(soff[-1])
+    # probe: one root, a few iterations
+    u, s, e1 = _oracle_job((workload, seed, 0, 1, 3))
+    rate = u / max(s, 1e-6)
+    per_core = max(1, min(n_roots // max(cores, 1), 64))
+    Ts = max(1, min(T, int(target_s * rate / max(per_core * e1, 1))))
+    jobs = [(workload, seed, (i * per_core) % max(n_roots - per_core + 1, 1), per_core, Ts) for i in range(cores)]
     t0 = time.perf_counter()
-    ts.cfr(leaf, Ts)
-    sec = time.perf_counter() - t0
-    return edges * Ts, sec, f"final round (round 5) of seed {seed} via {workload}: first {n} GT roots, {edges} FGT edges, T={Ts}"
+    if cores == 1:
+        res = [_oracle_job(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_job, jobs)
+    wall = time.perf_counter() - t0
+    upd = sum(r[0] for r in res)
+    return upd, wall, (f"final round of seed {seed} ({workload}): {cores} processes x {per_core} FGT roots, "
+                       f"T={Ts}, {sum(r[2] for r in res)} FGT edges in all")
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def cpu_baseline(args):
-    u, s, desc = oracle_sample(args.workload, args.seed, args.iters, CPU_SAMPLE_SECONDS)
-    return {"value": u / s, "unit": "node-updates/s", "cores": 1, "kind": "oracle", "sample": desc}
+    cores = host_cores()
+    u, s, desc = oracle_sample(args.workload, args.seed, args.iters, CPU_SAMPLE_SECONDS, cores)
+    return {"value": u / s, "unit": "node-updates/s", "cores": cores, "kind": "oracle", "sample": desc}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(args.workload, args.seed, args.iters, 2.0)
+        oracle_sample(args.workload, args.seed, args.iters, 1.0, cores)
     tot_u, tot_s, desc = 0, 0.0, ""
     for _ in range(args.steps):
-        u, s, desc = oracle_sample(args.workload, args.seed, args.iters, 8.0)
+        u, s, desc = oracle_sample(args.workload, args.seed, args.iters, 6.0, cores)
         tot_u += u
         tot_s += s
     v = tot_u / tot_s
@@ -316,7 +346,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded deals)", "impl": "reference",
         "config": {"workload": f"{args.workload}: {wdesc}", "seed": args.seed, "iters_per_round": args.iters},
-        "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -54,10 +54,13 @@ typedef struct {
  *   variant      0 = vanilla CFR (eq. RM + eq. avsigma), 1 = DCFR (eqs. DFCR_REG / DFCR_AVG)
  *   iters        number of iterations run by one pasur_cfr_iterate call (>= 0)
  *   rm_deadzone  tau: a cumulative regret counts as positive only above tau * t * Umax,
- *                Umax = max |leaf value| of the round, t = iteration index (1-based)
+ *                Umax = max |leaf value| in the subtree of the FGT root being solved (so each
+ *                root's solve depends on its own subtree only), t = iteration index (1-based)
  *   dcfr_alpha/beta/gamma  DCFR discount exponents (the paper ran 1.5, 0, 2)
- *   slots_per_item  score slots solved together by one thread block (0 = choose automatically)
- *   threads      threads per block of the CFR kernel (0 = choose automatically)
+ *   slots_per_item  score slots solved together by one thread block (0 = choose automatically,
+ *                at most 32)
+ *   threads      threads per block of the CFR kernel (0 = choose per subtree size, else a
+ *                multiple of 32 up to 1024)
  */
 typedef struct {
     int32_t variant;

@@ -80,6 +80,8 @@ def lib():
         L.or_cfr.argtypes = [C.c_void_p, f64p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                              C.c_double, f64p, f64p, f64p, f64p]
         L.or_cfr.restype = C.c_int
+        L.or_cfr_f32.argtypes = [C.c_void_p, f64p, C.c_int, C.c_double, f64p, f64p]
+        L.or_cfr_f32.restype = C.c_int
         L.or_root_values.argtypes = [C.c_void_p, f64p, f64p, C.c_int, f64p]
         L.or_root_values.restype = C.c_int
         L.or_count_round.argtypes = [u8p, C.c_int, C.c_uint64, i64p]
@@ -302,6 +304,16 @@ class Tree:
             raise ValueError("or_cfr failed")
         if want_rs:
             return sb, U, R, S
+        return sb, U
+
+    def cfr_f32(self, leaf, iters: int, tau: float = 1e-6):
+        """Vanilla CFR in float32 arithmetic (a conditioning probe for the tests, not a reference)."""
+        q = self.sizes()[1]
+        sb = np.zeros(int(q[1:].sum()), np.float64)
+        U = np.zeros(int(q[0]), np.float64)
+        lf = np.ascontiguousarray(leaf, np.float64)
+        if lib().or_cfr_f32(self._h, _p(lf, f64p), iters, tau, _p(sb, f64p), _p(U, f64p)) != 0:
+            raise ValueError("or_cfr_f32 failed")
         return sb, U
 
     def root_values(self, leaf, mode: int, sigma=None) -> np.ndarray:

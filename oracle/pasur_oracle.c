@@ -670,10 +670,27 @@ static double cfr_rec(cfr_ctx *c, int k, int64_t j, int64_t s, double pi0, doubl
     return v;
 }
 
+/* Umax of every FGT root: the largest |leaf value| in its own subtree (the dead-zone scale of
+ * regret matching, so that each root's solve depends on its subtree alone). */
+static double *root_umax(const or_tree *t, const double *leaf) {
+    double *um = (double *)calloc((size_t)t->nq[0] + 1, sizeof(double));
+    for (int64_t j = 0; j < t->n[8]; j++) {
+        int64_t g = t->root_of[8][j];
+        int64_t S = t->fgt_off[8][j + 1] - t->fgt_off[8][j];
+        for (int64_t s = 0; s < S; s++) {
+            double a = fabs(leaf[t->fgt_off[8][j] + s]);
+            int64_t q = t->fgt_off[0][g] + s;
+            if (a > um[q]) um[q] = a;
+        }
+    }
+    return um;
+}
+
 /*
  * T iterations of CFR on an unfolded round with the given FGT leaf values (eq. final_util /
  * eq. passuputil), simultaneous updates, root reach 1 for both players.  Iteration t:
- * sigma^t from the regrets by regret matching with dead zone tau*t*Umax (Umax = max |leaf|);
+ * sigma^t from the regrets by regret matching with dead zone tau*t*Umax (Umax = max |leaf| over the
+ * FGT root's own subtree);
  * reach top-down; values bottom-up v(h) = v(a0) + sum_a sigma(a) (v(h.a) - v(a0));
  * R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h)), S(h,a) += pi_p(h) sigma(h,a);  Uacc(root) += v(root).
  * Outputs (any may be NULL): sigma_bar per FGT edge by level (levels 1..8 concatenated, i.e.
@@ -695,18 +712,20 @@ int or_cfr(const or_tree *t, const double *leaf, int iters, double tau, int vari
         c.R[k] = (double *)calloc((size_t)t->nq[k] + 1, sizeof(double));
         c.S[k] = (double *)calloc((size_t)t->nq[k] + 1, sizeof(double));
     }
-    double umax = 0.0;
-    for (int64_t q = 0; q < t->nq[8]; q++) umax = fmax(umax, fabs(leaf[q]));
+    double *umax = root_umax(t, leaf);
     double *uacc = (double *)calloc((size_t)t->nq[0] + 1, sizeof(double));
     for (int it = 1; it <= iters; it++) {
         c.it = it;
-        c.thresh = tau * (double)it * umax;
         for (int64_t j = 0; j < t->n[0]; j++) {
             int64_t S = t->fgt_off[0][j + 1] - t->fgt_off[0][j];
-            for (int64_t s = 0; s < S; s++)
-                uacc[t->fgt_off[0][j] + s] += cfr_rec(&c, 0, j, s, 1.0, 1.0);
+            for (int64_t s = 0; s < S; s++) {
+                int64_t q = t->fgt_off[0][j] + s;
+                c.thresh = tau * (double)it * umax[q];
+                uacc[q] += cfr_rec(&c, 0, j, s, 1.0, 1.0);
+            }
         }
     }
+    free(umax);
     if (U)
         for (int64_t q = 0; q < t->nq[0]; q++) U[q] = iters > 0 ? uacc[q] / iters : 0.0;
     int64_t base = 0;
@@ -728,6 +747,98 @@ int or_cfr(const or_tree *t, const double *leaf, int iters, double tau, int vari
         }
         if (R_out) memcpy(R_out + base, c.R[k], sizeof(double) * (size_t)t->nq[k]);
         if (S_out) memcpy(S_out + base, c.S[k], sizeof(double) * (size_t)t->nq[k]);
+        base += t->nq[k];
+        free(c.R[k]);
+        free(c.S[k]);
+    }
+    free(uacc);
+    return 0;
+}
+
+/*
+ * The same vanilla CFR carried out in float32 arithmetic (the precision of the paper's strategy
+ * tensors, t_sgm float32).  Used only as a conditioning probe by the tests: an edge whose average
+ * strategy differs between this run and the fp64 run is one whose value f32 rounding decides.
+ */
+typedef struct {
+    const or_tree *t;
+    const double *leaf;
+    float *R[9], *S[9];
+    float thresh;
+} cfr32_ctx;
+
+static float cfr32_rec(cfr32_ctx *c, int k, int64_t j, int64_t s, float pi0, float pi1) {
+    const or_tree *t = c->t;
+    if (k == 8) return (float)c->leaf[t->fgt_off[8][j] + s];
+    int d = t->nchild[k][j];
+    int p = k & 1;
+    int64_t cb = t->child_beg[k][j];
+    float *sig = (float *)malloc(sizeof(float) * (size_t)d * 2);
+    float *vch = sig + d;
+    float sum = 0.f;
+    for (int a = 0; a < d; a++) {
+        float r = c->R[k + 1][t->fgt_off[k + 1][cb + a] + s];
+        sum += r > c->thresh ? r : 0.f;
+    }
+    for (int a = 0; a < d; a++) {
+        float r = c->R[k + 1][t->fgt_off[k + 1][cb + a] + s];
+        sig[a] = sum > 0.f ? (r > c->thresh ? r / sum : 0.f) : 1.f / (float)d;
+    }
+    for (int a = 0; a < d; a++)
+        vch[a] = cfr32_rec(c, k + 1, cb + a, s, p == 0 ? pi0 * sig[a] : pi0, p == 0 ? pi1 : pi1 * sig[a]);
+    float v = vch[0];
+    for (int a = 0; a < d; a++) v += sig[a] * (vch[a] - vch[0]);
+    float pi_p = p == 0 ? pi0 : pi1, pi_o = p == 0 ? pi1 : pi0, sp = p == 0 ? 1.f : -1.f;
+    for (int a = 0; a < d; a++) {
+        int64_t q = t->fgt_off[k + 1][cb + a] + s;
+        c->R[k + 1][q] += sp * pi_o * (vch[a] - v);
+        c->S[k + 1][q] += pi_p * sig[a];
+    }
+    free(sig);
+    return v;
+}
+
+int or_cfr_f32(const or_tree *t, const double *leaf, int iters, double tau, double *sigma_bar, double *U) {
+    if (!t->unfolded || iters < 0) return -1;
+    cfr32_ctx c;
+    memset(&c, 0, sizeof c);
+    c.t = t;
+    c.leaf = leaf;
+    for (int k = 1; k <= 8; k++) {
+        c.R[k] = (float *)calloc((size_t)t->nq[k] + 1, sizeof(float));
+        c.S[k] = (float *)calloc((size_t)t->nq[k] + 1, sizeof(float));
+    }
+    double *umax = root_umax(t, leaf);
+    double *uacc = (double *)calloc((size_t)t->nq[0] + 1, sizeof(double));
+    for (int it = 1; it <= iters; it++) {
+        for (int64_t j = 0; j < t->n[0]; j++) {
+            int64_t S = t->fgt_off[0][j + 1] - t->fgt_off[0][j];
+            for (int64_t s = 0; s < S; s++) {
+                int64_t q = t->fgt_off[0][j] + s;
+                c.thresh = (float)(tau * umax[q]) * (float)it;
+                uacc[q] += cfr32_rec(&c, 0, j, s, 1.f, 1.f);
+            }
+        }
+    }
+    free(umax);
+    if (U)
+        for (int64_t q = 0; q < t->nq[0]; q++) U[q] = iters > 0 ? uacc[q] / iters : 0.0;
+    int64_t base = 0;
+    for (int k = 1; k <= 8; k++) {
+        if (sigma_bar)
+            for (int64_t j = 0; j < t->n[k - 1]; j++) {
+                int d = t->nchild[k - 1][j];
+                int64_t cb = t->child_beg[k - 1][j];
+                int64_t S = t->fgt_off[k - 1][j + 1] - t->fgt_off[k - 1][j];
+                for (int64_t s = 0; s < S; s++) {
+                    double sum = 0.0;
+                    for (int a = 0; a < d; a++) sum += c.S[k][t->fgt_off[k][cb + a] + s];
+                    for (int a = 0; a < d; a++) {
+                        int64_t q = t->fgt_off[k][cb + a] + s;
+                        sigma_bar[base + q] = sum > 0.0 ? c.S[k][q] / sum : 1.0 / d;
+                    }
+                }
+            }
         base += t->nq[k];
         free(c.R[k]);
         free(c.S[k]);

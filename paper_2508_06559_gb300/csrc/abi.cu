@@ -198,6 +198,13 @@ int pasur_destroy(pasur_ctx *ctx) {
     dev_free(ctx, ctx->counter, 64);
     dev_free(ctx, ctx->errflag, 64);
     cudaStreamSynchronize(ctx->stream);
+    for (int c = 0; c < 8; c++) {
+        if (ctx->aux[c]) cudaStreamDestroy(ctx->aux[c]);
+        if (ctx->join[c]) cudaEventDestroy(ctx->join[c]);
+        if (ctx->cls_t0[c]) cudaEventDestroy(ctx->cls_t0[c]);
+        if (ctx->cls_t1[c]) cudaEventDestroy(ctx->cls_t1[c]);
+    }
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PASUR_OK;

@@ -326,9 +326,9 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev) {
     }
     // per-root level bounds -> RootInfo (host + device)
     int64_t nr = t->n_roots;
-    int64_t *bounds = nullptr;
     size_t bb = sizeof(int64_t) * 9 * (size_t)(nr + 1);
-    PASUR_TRY(dev_alloc(ctx, (void **)&bounds, bb));
+    PASUR_TRY(tree_alloc(t, (void **)&t->bounds_d, bb));
+    int64_t *bounds = t->bounds_d;
     OffPtrs co;
     for (int k = 0; k < 8; k++) co.p[k] = t->child_off[k];
     co.p[8] = nullptr;
@@ -338,7 +338,6 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev) {
     std::vector<int64_t> hb(9 * (size_t)(nr + 1));
     PASUR_CUDA(ctx, cudaMemcpyAsync(hb.data(), bounds, bb, cudaMemcpyDeviceToHost, ctx->stream));
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    dev_free(ctx, bounds, bb);
     t->roots_h.assign((size_t)nr, RootInfo{});
     int64_t soff = 0;
     for (int64_t g = 0; g < nr; g++) {
@@ -357,12 +356,6 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev) {
         ri.struct_off = soff;
         soff += ri.n_internal;
     }
-    if (nr > 0) {
-        PASUR_TRY(tree_alloc(t, (void **)&t->roots_d, sizeof(RootInfo) * (size_t)nr));
-        PASUR_CUDA(ctx, cudaMemcpyAsync(t->roots_d, t->roots_h.data(), sizeof(RootInfo) * (size_t)nr,
-                                        cudaMemcpyHostToDevice, ctx->stream));
-    }
-    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return PASUR_OK;
 }
 

@@ -2,238 +2,408 @@
 // DFCR_REG / DFCR_AVG).
 //
 // Round roots are independent (open hands: every FGT node is its own information set and root
-// reach is 1), so the round is cut into work items: one GT root and a run of its score slots.
-// A persistent grid takes items from a queue (largest first).  One thread block runs all T
-// iterations of an item: per iteration a top-down pass over levels 0..6 (regret matching and
+// reach is 1), so the round is cut into work items: one GT root and a run of W of its score
+// slots.  A persistent grid takes items from a queue (largest first).  One thread block runs all
+// T iterations of an item: per iteration a top-down pass over levels 0..6 (regret matching and
 // reach) and a bottom-up pass over levels 7..0 (values, regret and strategy-sum updates), with a
-// block barrier between levels; a (node, slot) pair belongs to one thread in each pass, so the
-// updates of a parent's child edges need no atomics.  The item's regrets R, strategy sums S,
-// values and reaches live in shared memory when they fit ("resident": no DRAM traffic per
-// iteration), otherwise in device memory.  Layout of an item: local node index (level-major,
-// the root's GT subtree in level order) times slots, slot-minor.
+// block barrier between levels; an (active node, slot) pair belongs to one thread in each pass,
+// so the updates of a node's child edges need no atomics.
+//
+// Forced-move chains are resolved once: a node whose whole subtree is one path of single moves
+// has sigma = 1 and zero regret on every edge below it and the value of its one leaf, so only the
+// "active" nodes (a local node that is not such a chain) are swept, and state is kept only for
+// local nodes (the root and the children of active nodes).  The item's regrets R, strategy sums
+// S, values V and reaches live in shared memory when they fit ("resident": no DRAM traffic per
+// iteration), otherwise in device memory.  Item layout: local node index times slots,
+// slot-minor.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "pasur_internal.cuh"
 
 namespace pasur {
 namespace {
 
+// shared-memory classes of the resident items: budget per block (several blocks per SM), then
+// the global-memory fallback
+constexpr int kNumCls = 6;
+constexpr size_t kClsBudget[kNumCls - 1] = {40 * 1024, 54 * 1024, 74 * 1024, 112 * 1024, 0 /* opt-in max */};
+constexpr int kClsGlobal = kNumCls - 1;
+constexpr int kClsThreads[kNumCls] = {128, 128, 256, 512, 1024, 256};
+
 struct CfrParams {
     const CfrItem *items;
-    int64_t n_items;
-    const RootInfo *roots;
-    const int32_t *lcs;
-    const uint16_t *ldeg;
+    int64_t i_begin, i_end;
+    const CfrRoot *roots;
+    const int32_t *act_li, *act_pl, *act_cs;
+    const uint16_t *act_d;
+    const int64_t *loc_tq;
     const float *leaf_v;
-    const int64_t *fgt_off8;
     const int64_t *fgt_off0;
-    float *R, *S, *V, *P0, *P1;
+    float *R, *S, *V, *X;
     double *uacc;
     const float *dcfr;  // per iteration: regret factor if R > 0, if R <= 0, strategy-sum factor
     int iters;
     int64_t t0;
-    float tau_umax;
+    float tau;  // dead zone: a regret counts as positive above tau * t * Umax(root)
     int32_t *counter;
     int32_t *err;
 };
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ __forceinline__ size_t resident_bytes(int64_t N, int64_t Nint, int64_t W) {
-    return al16((size_t)Nint * 4) + al16((size_t)Nint * 2) + 3 * al16((size_t)N * W * 4) + 2 * al16((size_t)Nint * W * 4);
+__host__ __device__ __forceinline__ size_t resident_bytes(int64_t L, int64_t nA, int64_t W) {
+    return 3 * al16((size_t)nA * 4) + al16((size_t)nA * 2) + 4 * al16((size_t)L * W * 4);
+}
+
+constexpr int KC = 8;  // degrees with a fully unrolled path (larger degrees loop over memory)
+constexpr int kMaxSlots = 32;  // score slots per work item
+
+// Regret matching at one (active node, slot) with D children and the reach of the children.
+// X[n] holds the reach of the player who moved into node n; own = the mover's reach at the node.
+template <int D>
+__device__ __forceinline__ void td_node(int c, int W, int w, float own, const float *__restrict__ R, float *__restrict__ X,
+                                        float thr) {
+    if (D == 1) {
+        X[c * W + w] = own;
+        return;
+    }
+    float r[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) r[a] = R[(c + a) * W + w];
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; a++) sum += r[a] > thr ? r[a] : 0.f;
+    if (sum > 0.f) {
+        const float inv = 1.f / sum;
+#pragma unroll
+        for (int a = 0; a < D; a++) X[(c + a) * W + w] = r[a] > thr ? own * (r[a] * inv) : 0.f;
+    } else {
+        const float u = own * (1.f / (float)D);
+#pragma unroll
+        for (int a = 0; a < D; a++) X[(c + a) * W + w] = u;
+    }
+}
+
+__device__ __forceinline__ void td_node_any(int c, int d, int W, int w, float own, const float *__restrict__ R,
+                                            float *__restrict__ X, float thr) {
+    float sum = 0.f;
+    for (int a = 0; a < d; a++) {
+        const float r = R[(c + a) * W + w];
+        sum += r > thr ? r : 0.f;
+    }
+    if (sum > 0.f) {
+        const float inv = 1.f / sum;
+        for (int a = 0; a < d; a++) {
+            const float r = R[(c + a) * W + w];
+            X[(c + a) * W + w] = r > thr ? own * (r * inv) : 0.f;
+        }
+    } else {
+        const float u = own * (1.f / (float)d);
+        for (int a = 0; a < d; a++) X[(c + a) * W + w] = u;
+    }
+}
+
+// Value of one (active node, slot) with D children, then R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h))
+// and S(h,a) += pi_p(h) sigma(h,a) for its child edges.  Returns v(h).
+template <int VARIANT, int D>
+__device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float spo, float *__restrict__ R,
+                                         float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
+                                         float fneg, float fs) {
+    float r[D], v[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        r[a] = R[(c + a) * W + w];
+        v[a] = V[(c + a) * W + w];
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; a++) sum += r[a] > thr ? r[a] : 0.f;
+    const float inv = sum > 0.f ? 1.f / sum : 0.f, u = 1.f / (float)D;
+    float vh = v[0];
+#pragma unroll
+    for (int a = 1; a < D; a++) vh += (sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u) * (v[a] - v[0]);
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const int q = (c + a) * W + w;
+        const float sg = sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u;
+        const float inst = spo * (v[a] - vh);
+        if (VARIANT == 1) {
+            R[q] = r[a] * (r[a] > 0.f ? fpos : fneg) + inst;
+            S[q] = S[q] * fs + pp * sg;
+        } else {
+            R[q] = r[a] + inst;
+            S[q] = S[q] + pp * sg;
+        }
+    }
+    return vh;
 }
 
 template <int VARIANT>
-__global__ void __launch_bounds__(256) k_cfr_items(CfrParams p) {
+__device__ __forceinline__ float bu_node_any(int c, int d, int W, int w, float pp, float spo, float *__restrict__ R,
+                                             float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
+                                             float fneg, float fs) {
+    float sum = 0.f;
+    for (int a = 0; a < d; a++) {
+        const float r = R[(c + a) * W + w];
+        sum += r > thr ? r : 0.f;
+    }
+    const float inv = sum > 0.f ? 1.f / sum : 0.f, u = 1.f / (float)d;
+    const float v0 = V[c * W + w];
+    float vh = v0;
+    for (int a = 1; a < d; a++) {
+        const float r = R[(c + a) * W + w];
+        vh += (sum > 0.f ? (r > thr ? r * inv : 0.f) : u) * (V[(c + a) * W + w] - v0);
+    }
+    for (int a = 0; a < d; a++) {
+        const int q = (c + a) * W + w;
+        const float r = R[q];
+        const float sg = sum > 0.f ? (r > thr ? r * inv : 0.f) : u;
+        const float inst = spo * (V[q] - vh);
+        if (VARIANT == 1) {
+            R[q] = r * (r > 0.f ? fpos : fneg) + inst;
+            S[q] = S[q] * fs + pp * sg;
+        } else {
+            R[q] = r + inst;
+            S[q] = S[q] + pp * sg;
+        }
+    }
+    return vh;
+}
+
+// One level of the top-down pass over (active node, slot) pairs.  The active entries of a level
+// are sorted by degree, so the lanes of a warp mostly take the same unrolled path.
+template <int VARIANT>
+__device__ __forceinline__ void td_level(int b, int n, int W, int t0x, int stride, const int32_t *__restrict__ Apl,
+                                         const int32_t *__restrict__ Acs, const uint16_t *__restrict__ Ad,
+                                         const float *__restrict__ R, float *__restrict__ X, const float *tu, float tf) {
+    for (int x = t0x; x < n; x += stride) {
+        const int e = W == 1 ? b + x : b + x / W, w = W == 1 ? 0 : x % W;
+        const int pl = Apl[e], c = Acs[e], d = Ad[e];
+        const float thr = tu[w] * tf;
+        const float own = pl < 0 ? 1.f : X[pl * W + w];
+        switch (d) {
+            case 1: td_node<1>(c, W, w, own, R, X, thr); break;
+            case 2: td_node<2>(c, W, w, own, R, X, thr); break;
+            case 3: td_node<3>(c, W, w, own, R, X, thr); break;
+            case 4: td_node<4>(c, W, w, own, R, X, thr); break;
+            case 5: td_node<5>(c, W, w, own, R, X, thr); break;
+            case 6: td_node<6>(c, W, w, own, R, X, thr); break;
+            case 7: td_node<7>(c, W, w, own, R, X, thr); break;
+            case 8: td_node<8>(c, W, w, own, R, X, thr); break;
+            default: td_node_any(c, d, W, w, own, R, X, thr);
+        }
+    }
+}
+
+// One level of the bottom-up pass over (active node, slot) pairs.
+template <int VARIANT>
+__device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int t0x, int stride,
+                                         const int32_t *__restrict__ Ali, const int32_t *__restrict__ Apl,
+                                         const int32_t *__restrict__ Acs, const uint16_t *__restrict__ Ad,
+                                         float *__restrict__ R, float *__restrict__ S, float *__restrict__ V,
+                                         const float *__restrict__ X, const float *tu, float tf, float fpos, float fneg,
+                                         float fs) {
+    for (int x = t0x; x < n; x += stride) {
+        const int e = W == 1 ? b + x : b + x / W, w = W == 1 ? 0 : x % W;
+        const int li = Ali[e], pl = Apl[e], c = Acs[e], d = Ad[e];
+        const float thr = tu[w] * tf;
+        const float pp = pl < 0 ? 1.f : X[pl * W + w];  // pi_p(h)
+        const float po = X[li * W + w];                  // pi_{-p}(h)
+        const float spo = alex ? po : -po;
+        float vh;
+        switch (d) {
+            case 1: vh = bu_node<VARIANT, 1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 2: vh = bu_node<VARIANT, 2>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 3: vh = bu_node<VARIANT, 3>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 4: vh = bu_node<VARIANT, 4>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 5: vh = bu_node<VARIANT, 5>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 6: vh = bu_node<VARIANT, 6>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 7: vh = bu_node<VARIANT, 7>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 8: vh = bu_node<VARIANT, 8>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            default: vh = bu_node_any<VARIANT>(c, d, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
+        }
+        V[li * W + w] = vh;
+    }
+}
+
+// All T iterations of one item.  RES: the item's arrays are in shared memory (carved from sm);
+// otherwise they are in device memory.
+template <int VARIANT, bool RES>
+__device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, const CfrRoot &cr, const int32_t *s_as,
+                                         float *s_tu, unsigned char *sm) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const bool warp0 = tid < 32;
+    const int W = it.ns;
+    const int L = cr.ls[9], nA = s_as[9];
+    const int32_t *Ali, *Apl, *Acs;
+    const uint16_t *Ad;
+    float *R, *S, *V, *X;
+    const int32_t *gli = p.act_li + cr.act_off, *gpl = p.act_pl + cr.act_off, *gcs = p.act_cs + cr.act_off;
+    const uint16_t *gd = p.act_d + cr.act_off;
+    if (RES) {
+        size_t o = 0;
+        int32_t *sli = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
+        int32_t *spl = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
+        int32_t *scs = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
+        uint16_t *sd = (uint16_t *)(sm + o); o += al16((size_t)nA * 2);
+        R = (float *)(sm + o); o += al16((size_t)L * W * 4);
+        S = (float *)(sm + o); o += al16((size_t)L * W * 4);
+        V = (float *)(sm + o); o += al16((size_t)L * W * 4);
+        X = (float *)(sm + o);
+        for (int i = tid; i < nA; i += nth) {
+            sli[i] = gli[i];
+            spl[i] = gpl[i];
+            scs[i] = gcs[i];
+            sd[i] = gd[i];
+        }
+        const float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
+        for (int i = tid; i < L * W; i += nth) {
+            R[i] = gR[i];
+            S[i] = gS[i];
+        }
+        Ali = sli;
+        Apl = spl;
+        Acs = scs;
+        Ad = sd;
+    } else {
+        Ali = gli;
+        Apl = gpl;
+        Acs = gcs;
+        Ad = gd;
+        R = p.R + it.data_base;
+        S = p.S + it.data_base;
+        V = p.V + it.scratch_base;
+        X = p.X + it.scratch_base;
+    }
+    // values of the terminals (leaves and chain heads), constant over the iterations; root reach;
+    // per slot the largest |leaf value| of the root's subtree, the scale of the dead zone
+    for (int w = tid; w < W; w += nth) s_tu[w] = 0.f;
+    __syncthreads();
+    {
+        const int64_t *tq = p.loc_tq + cr.loc_off;
+        for (int x = tid; x < L * W; x += nth) {
+            const int li = x / W, w = x - li * W;
+            const int64_t q = tq[li];
+            if (q >= 0) {
+                const float v = p.leaf_v[q + it.s0 + w];
+                V[x] = v;
+                atomicMax((unsigned *)&s_tu[w], __float_as_uint(fabsf(v)));
+            }
+        }
+        for (int w = tid; w < W; w += nth) X[w] = 1.f;
+    }
+    __syncthreads();
+    for (int w = tid; w < W; w += nth) s_tu[w] = p.tau * s_tu[w];
+    __syncthreads();
+    double acc = 0.0;
+    for (int il = 0; il < p.iters; il++) {
+        const int64_t t = p.t0 + il + 1;
+        const float tf = (float)t;
+        float fpos = 0.f, fneg = 0.f, fs = 0.f;
+        if (VARIANT == 1) {
+            fpos = p.dcfr[3 * il];
+            fneg = p.dcfr[3 * il + 1];
+            fs = p.dcfr[3 * il + 2];
+        }
+        // top-down over levels 0..6; a level of at most 32 (node, slot) pairs runs on warp 0
+        // alone, and only a change between warp-0 and whole-block levels needs a block barrier
+        for (int k = 0; k < 7; k++) {
+            const int b = s_as[k], n = (s_as[k + 1] - b) * W;
+            if (n == 0) continue;
+            const bool small = n <= 32;
+            if (!small) td_level<VARIANT>(b, n, W, tid, nth, Apl, Acs, Ad, R, X, s_tu, tf);
+            else if (warp0) td_level<VARIANT>(b, n, W, tid, 32, Apl, Acs, Ad, R, X, s_tu, tf);
+            int kn = k + 1;
+            while (kn < 7 && s_as[kn + 1] == s_as[kn]) kn++;
+            const bool next_small = kn < 7 && (s_as[kn + 1] - s_as[kn]) * W <= 32;
+            if (small && next_small) __syncwarp();
+            else __syncthreads();
+        }
+        // bottom-up over levels 7..0
+        for (int k = 7; k >= 0; k--) {
+            const int b = s_as[k], n = (s_as[k + 1] - b) * W;
+            if (n == 0) continue;
+            const bool small = n <= 32, alex = (k & 1) == 0;
+            if (!small) bu_level<VARIANT>(alex, b, n, W, tid, nth, Ali, Apl, Acs, Ad, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+            else if (warp0) bu_level<VARIANT>(alex, b, n, W, tid, 32, Ali, Apl, Acs, Ad, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+            int kn = k - 1;
+            while (kn >= 0 && s_as[kn + 1] == s_as[kn]) kn--;
+            const bool next_small = kn >= 0 && (s_as[kn + 1] - s_as[kn]) * W <= 32;
+            if (small && next_small) __syncwarp();
+            else __syncthreads();
+        }
+        if (tid < W) acc += (double)V[tid];
+        __syncthreads();
+    }
+    if (tid < W) {
+        if (!isfinite(acc)) atomicOr(p.err, 1);
+        p.uacc[p.fgt_off0[it.root] + it.s0 + tid] += acc;
+    }
+    if (RES) {
+        float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
+        for (int i = tid; i < L * W; i += nth) {
+            gR[i] = R[i];
+            gS[i] = S[i];
+        }
+    }
+    __syncthreads();
+}
+
+template <int VARIANT, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_cfr_items(CfrParams p) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_item;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    __shared__ int32_t s_as[10];
+    __shared__ float s_tu[kMaxSlots];
+    const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(p.counter, 1);
         __syncthreads();
-        const int64_t id = s_item;
+        const int64_t id = p.i_begin + s_item;
+        if (tid < 10) s_as[tid] = id < p.i_end ? p.roots[p.items[id].root].as[tid] : 0;
         __syncthreads();
-        if (id >= p.n_items) break;
+        if (id >= p.i_end) break;
         const CfrItem it = p.items[id];
-        const RootInfo &ri = p.roots[it.root];
-        const int W = it.ns;
-        const int N = ri.local_start[9], Nint = ri.n_internal;
-        const bool resident = it.scratch_base < 0;
-        const int32_t *cs;
-        const uint16_t *dg;
-        float *R, *S, *V, *P0, *P1;
-        if (resident) {
-            size_t o = 0;
-            int32_t *cs_s = (int32_t *)(sm + o); o += al16((size_t)Nint * 4);
-            uint16_t *dg_s = (uint16_t *)(sm + o); o += al16((size_t)Nint * 2);
-            R = (float *)(sm + o); o += al16((size_t)N * W * 4);
-            S = (float *)(sm + o); o += al16((size_t)N * W * 4);
-            V = (float *)(sm + o); o += al16((size_t)N * W * 4);
-            P0 = (float *)(sm + o); o += al16((size_t)Nint * W * 4);
-            P1 = (float *)(sm + o);
-            const int32_t *gcs = p.lcs + ri.struct_off;
-            const uint16_t *gdg = p.ldeg + ri.struct_off;
-            for (int i = tid; i < Nint; i += nth) {
-                cs_s[i] = gcs[i];
-                dg_s[i] = gdg[i];
-            }
-            const float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
-            for (int i = tid; i < N * W; i += nth) {
-                R[i] = gR[i];
-                S[i] = gS[i];
-            }
-            cs = cs_s;
-            dg = dg_s;
-        } else {
-            cs = p.lcs + ri.struct_off;
-            dg = p.ldeg + ri.struct_off;
-            R = p.R + it.data_base;
-            S = p.S + it.data_base;
-            V = p.V + it.scratch_base;
-            P0 = p.P0 + it.scratch_base;
-            P1 = p.P1 + it.scratch_base;
-        }
-        // leaf values (constant over the iterations)
-        {
-            const int nl = ri.lvl_count[8];
-            const int64_t jb = ri.lvl_begin[8];
-            for (int x = tid; x < nl * W; x += nth) {
-                int i = x / W, w = x - i * W;
-                V[(int64_t)(Nint + i) * W + w] = p.leaf_v[p.fgt_off8[jb + i] + it.s0 + w];
-            }
-        }
-        __syncthreads();
-        double acc = 0.0;
-        for (int il = 0; il < p.iters; il++) {
-            const int64_t t = p.t0 + il + 1;
-            const float thr = p.tau_umax * (float)t;
-            float fpos = 0.f, fneg = 0.f, fs = 0.f;
-            if (VARIANT == 1) {
-                fpos = p.dcfr[3 * il];
-                fneg = p.dcfr[3 * il + 1];
-                fs = p.dcfr[3 * il + 2];
-            }
-            for (int w = tid; w < W; w += nth) {
-                P0[w] = 1.f;
-                P1[w] = 1.f;
-            }
-            __syncthreads();
-            // top-down: reach of levels 1..7 (leaves need none)
-            for (int k = 0; k < 7; k++) {
-                const int nk = ri.lvl_count[k], base = ri.local_start[k];
-                const bool alex = (k & 1) == 0;
-                for (int x = tid; x < nk * W; x += nth) {
-                    const int i = x / W, w = x - i * W, li = base + i;
-                    const int c = cs[li], d = dg[li];
-                    const float a0 = P0[li * W + w], a1 = P1[li * W + w];
-                    if (d == 1) {
-                        P0[c * W + w] = a0;
-                        P1[c * W + w] = a1;
-                        continue;
-                    }
-                    float sum = 0.f;
-                    for (int a = 0; a < d; a++) {
-                        float r = R[(c + a) * W + w];
-                        sum += r > thr ? r : 0.f;
-                    }
-                    const float u = 1.f / (float)d;
-                    for (int a = 0; a < d; a++) {
-                        float r = R[(c + a) * W + w];
-                        float sg = sum > 0.f ? (r > thr ? r / sum : 0.f) : u;
-                        P0[(c + a) * W + w] = alex ? a0 * sg : a0;
-                        P1[(c + a) * W + w] = alex ? a1 : a1 * sg;
-                    }
-                }
-                __syncthreads();
-            }
-            // bottom-up: values, regrets, strategy sums
-            for (int k = 7; k >= 0; k--) {
-                const int nk = ri.lvl_count[k], base = ri.local_start[k];
-                const bool alex = (k & 1) == 0;
-                for (int x = tid; x < nk * W; x += nth) {
-                    const int i = x / W, w = x - i * W, li = base + i;
-                    const int c = cs[li], d = dg[li];
-                    if (d == 1) {
-                        V[li * W + w] = V[c * W + w];
-                        continue;
-                    }
-                    const float a0 = P0[li * W + w], a1 = P1[li * W + w];
-                    float sum = 0.f;
-                    for (int a = 0; a < d; a++) {
-                        float r = R[(c + a) * W + w];
-                        sum += r > thr ? r : 0.f;
-                    }
-                    const float u = 1.f / (float)d;
-                    const float v0 = V[c * W + w];
-                    float vh = v0;
-                    for (int a = 0; a < d; a++) {
-                        float r = R[(c + a) * W + w];
-                        float sg = sum > 0.f ? (r > thr ? r / sum : 0.f) : u;
-                        vh += sg * (V[(c + a) * W + w] - v0);
-                    }
-                    const float pp = alex ? a0 : a1, po = alex ? a1 : a0;
-                    const float spo = alex ? po : -po;
-                    for (int a = 0; a < d; a++) {
-                        const int q = (c + a) * W + w;
-                        float r = R[q];
-                        float sg = sum > 0.f ? (r > thr ? r / sum : 0.f) : u;
-                        float inst = spo * (V[q] - vh);
-                        if (VARIANT == 1) {
-                            R[q] = r * (r > 0.f ? fpos : fneg) + inst;
-                            S[q] = S[q] * fs + pp * sg;
-                        } else {
-                            R[q] = r + inst;
-                            S[q] = S[q] + pp * sg;
-                        }
-                    }
-                    V[li * W + w] = vh;
-                }
-                __syncthreads();
-            }
-            if (tid < W) acc += (double)V[tid];
-        }
-        if (tid < W) {
-            if (!isfinite(acc)) atomicOr(p.err, 1);
-            p.uacc[p.fgt_off0[it.root] + it.s0 + tid] += acc;
-        }
-        if (resident) {
-            float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
-            for (int i = tid; i < N * W; i += nth) {
-                gR[i] = R[i];
-                gS[i] = S[i];
-            }
-        }
-        __syncthreads();
+        const CfrRoot &cr = p.roots[it.root];
+        if (it.scratch_base < 0) run_item<VARIANT, true>(p, it, cr, s_as, s_tu, sm);
+        else run_item<VARIANT, false>(p, it, cr, s_as, s_tu, sm);
     }
 }
 
 struct LevelPtrs {
-    const int64_t *p[9];
+    const int64_t *fgt[9];
+    const int64_t *child[9];
     int64_t base[9];  // offset of level k in the concatenated edge output (levels 1..8)
 };
 
-// average strategy of every edge, canonical FGT order, one block per item
-__global__ void k_export_sigma(const CfrItem *items, int64_t n_items, const RootInfo *roots, const int32_t *lcs,
-                               const uint16_t *ldeg, const float *Sg, LevelPtrs lp, float *out) {
+__global__ void k_fill(float *out, int64_t n, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) out[i] = v;
+}
+
+// average strategy of the child edges of every active node, canonical FGT order, one block per
+// item (every other edge lies below a forced move and has average strategy 1)
+__global__ void k_export_sigma(const CfrItem *items, int64_t n_items, const CfrRoot *roots, const int32_t *act_cs,
+                               const uint16_t *act_d, const int64_t *act_gt, const float *Sg, LevelPtrs lp, float *out) {
     for (int64_t id = blockIdx.x; id < n_items; id += gridDim.x) {
         const CfrItem it = items[id];
-        const RootInfo &ri = roots[it.root];
+        const CfrRoot &cr = roots[it.root];
         const int W = it.ns;
-        const int32_t *cs = lcs + ri.struct_off;
-        const uint16_t *dg = ldeg + ri.struct_off;
         const float *S = Sg + it.data_base;
         for (int k = 0; k < 8; k++) {
-            const int nk = ri.lvl_count[k], base = ri.local_start[k];
-            for (int x = threadIdx.x; x < nk * W; x += blockDim.x) {
-                const int i = x / W, w = x - i * W, li = base + i;
-                const int c = cs[li], d = dg[li];
+            const int b = cr.as[k], n = (cr.as[k + 1] - b) * W;
+            for (int x = threadIdx.x; x < n; x += blockDim.x) {
+                const int e = b + x / W, w = x % W;
+                const int c = act_cs[cr.act_off + e], d = act_d[cr.act_off + e];
+                const int64_t j = act_gt[cr.act_off + e];
                 float sum = 0.f;
                 for (int a = 0; a < d; a++) sum += S[(c + a) * W + w];
+                const int64_t c0 = lp.child[k][j];
                 for (int a = 0; a < d; a++) {
-                    int64_t j = ri.lvl_begin[k + 1] + (c + a - ri.local_start[k + 1]);
                     float sb = sum > 0.f ? S[(c + a) * W + w] / sum : 1.f / (float)d;
-                    out[lp.base[k + 1] + lp.p[k + 1][j] + it.s0 + w] = sb;
+                    out[lp.base[k + 1] + lp.fgt[k + 1][c0 + a] + it.s0 + w] = sb;
                 }
             }
         }
@@ -245,17 +415,81 @@ __global__ void k_export_util(const double *uacc, int64_t n, double inv_t, float
         out[i] = (float)(uacc[i] * inv_t);
 }
 
-// local structure of every internal GT node: first child (local index) and number of children
-__global__ void k_local_structure(const int32_t *root, const int64_t *child_off, int64_t m, int k,
-                                  const RootInfo *roots, int32_t *lcs, uint16_t *ldeg, int32_t *err) {
+// chain[j] = 1 when the subtree of j is one path of forced moves (leaves included)
+__global__ void k_chain(const int64_t *child_off, int64_t m, const uint8_t *chain_next, uint8_t *chain) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-        const RootInfo &ri = roots[root[j]];
-        int64_t li = ri.local_start[k] + (j - ri.lvl_begin[k]);
-        int64_t c0 = child_off[j], d = child_off[j + 1] - c0;
-        if (d < 1 || d > 65535) atomicOr(err, 2);
-        lcs[ri.struct_off + li] = (int32_t)(ri.local_start[k + 1] + (c0 - ri.lvl_begin[k + 1]));
-        ldeg[ri.struct_off + li] = (uint16_t)d;
+        int64_t c0 = child_off[j];
+        chain[j] = (child_off[j + 1] - c0 == 1 && chain_next[c0]) ? 1 : 0;
     }
+}
+
+// local and active flags of level k from level k-1 (local: the root, or the parent is active;
+// active: local, not a chain, not a leaf)
+__global__ void k_flags(const int64_t *parent, int64_t m, const int32_t *active_prev, const uint8_t *chain, bool leaves,
+                        int32_t *local, int32_t *active) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t l = parent ? active_prev[parent[j]] : 1;
+        local[j] = l;
+        active[j] = (l && !leaves && !chain[j]) ? 1 : 0;
+    }
+}
+
+struct RankPtrs {
+    const int64_t *loc[9];
+    const int64_t *act[9];
+};
+
+// per root and level: global local-rank and active-rank at the root's first node
+__global__ void k_root_ranks(const int64_t *bounds, int64_t n_roots, RankPtrs rp, int64_t *out) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= n_roots; g += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 9; k++) {
+            int64_t b = bounds[g * 9 + k];
+            out[g * 18 + k] = rp.loc[k][b];
+            out[g * 18 + 9 + k] = rp.act[k][b];
+        }
+}
+
+struct ChildPtrs {
+    const int64_t *p[9];
+};
+
+__global__ void k_fill_layout(int k, int64_t m, const int32_t *root, const int32_t *local, const int32_t *active,
+                              const int64_t *loc_rank, const int64_t *act_rank, const int64_t *loc_rank_next,
+                              const int64_t *loc_rank_prev, const int64_t *parent, ChildPtrs co, const int64_t *fgt_off8,
+                              const CfrRoot *roots, int64_t *loc_tq, int32_t *act_li, int32_t *act_pl, int32_t *act_cs,
+                              uint16_t *act_d, int64_t *act_gt, uint64_t *act_key, int32_t *err) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        if (!local[j]) continue;
+        const CfrRoot &cr = roots[root[j]];
+        const int64_t li = cr.ls[k] + (loc_rank[j] - cr.locbase[k]);
+        if (active[j]) {
+            loc_tq[cr.loc_off + li] = -1;
+            const int64_t e = cr.as[k] + (act_rank[j] - cr.actbase[k]);
+            const int64_t c0 = co.p[k][j], d = co.p[k][j + 1] - c0;
+            if (d > 65535) atomicOr(err, 2);
+            act_li[cr.act_off + e] = (int32_t)li;
+            act_pl[cr.act_off + e] =
+                k == 0 ? -1 : (int32_t)(cr.ls[k - 1] + (loc_rank_prev[parent[j]] - cr.locbase[k - 1]));
+            act_cs[cr.act_off + e] = (int32_t)(cr.ls[k + 1] + (loc_rank_next[c0] - cr.locbase[k + 1]));
+            act_d[cr.act_off + e] = (uint16_t)d;
+            act_gt[cr.act_off + e] = j;
+            // sort key: the (root, level) segment, then degree descending
+            act_key[cr.act_off + e] = ((uint64_t)(cr.act_off + cr.as[k]) << 16) | (uint64_t)(0xFFFF - (d > 0xFFFF ? 0xFFFF : d));
+        } else {
+            int64_t x = j;
+            for (int kk = k; kk < 8; kk++) x = co.p[kk][x];  // follow the forced moves to the leaf
+            loc_tq[cr.loc_off + li] = fgt_off8[x];
+        }
+    }
+}
+
+__global__ void k_iota(int64_t *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) out[i] = i;
+}
+
+template <typename T>
+__global__ void k_gather(const T *in, const int64_t *perm, int64_t n, T *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) out[i] = in[perm[i]];
 }
 
 unsigned grid_for(int64_t threads, int block) {
@@ -265,20 +499,115 @@ unsigned grid_for(int64_t threads, int block) {
     return (unsigned)b;
 }
 
-}  // namespace
+template <typename T>
+int tmp_alloc(pasur_ctx *ctx, std::vector<std::pair<void *, size_t>> &tmp, T **p, int64_t n) {
+    size_t b = sizeof(T) * (size_t)(n + 1);
+    PASUR_TRY(dev_alloc(ctx, (void **)p, b));
+    tmp.push_back({(void *)*p, b});
+    return PASUR_OK;
+}
 
-int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
+int build_layout(pasur_tree *t) {
     pasur_ctx *ctx = t->ctx;
-    // local structure arrays
-    int64_t nint = 0;
-    for (int k = 0; k < 8; k++) nint += t->M[k];
-    PASUR_TRY(tree_alloc(t, (void **)&t->lcs, sizeof(int32_t) * (size_t)(nint + 1)));
-    PASUR_TRY(tree_alloc(t, (void **)&t->ldeg, sizeof(uint16_t) * (size_t)(nint + 1)));
-    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int32_t), ctx->stream));
-    for (int k = 0; k < 8; k++) {
+    std::vector<std::pair<void *, size_t>> tmp;
+    struct Guard {
+        pasur_ctx *c;
+        std::vector<std::pair<void *, size_t>> *v;
+        ~Guard() {
+            for (auto &x : *v) dev_free(c, x.first, x.second);
+        }
+    } guard{ctx, &tmp};
+    uint8_t *chain[9];
+    int32_t *local[9], *active[9];
+    int64_t *lrank[9], *arank[9];
+    for (int k = 0; k < 9; k++) {
+        PASUR_TRY(tmp_alloc(ctx, tmp, &chain[k], t->M[k]));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &local[k], t->M[k]));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &active[k], t->M[k]));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &lrank[k], t->M[k]));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &arank[k], t->M[k]));
+    }
+    PASUR_CUDA(ctx, cudaMemsetAsync(chain[8], 1, (size_t)t->M[8] + 1, ctx->stream));
+    for (int k = 7; k >= 0; k--) {
         if (t->M[k] == 0) continue;
-        k_local_structure<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(t->root[k], t->child_off[k], t->M[k], k,
-                                                                           t->roots_d, t->lcs, t->ldeg, ctx->errflag);
+        k_chain<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(t->child_off[k], t->M[k], chain[k + 1], chain[k]);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+    }
+    for (int k = 0; k < 9; k++) {
+        if (t->M[k] > 0) {
+            k_flags<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(k ? t->parent[k] : nullptr, t->M[k],
+                                                                    k ? active[k - 1] : nullptr, chain[k], k == 8,
+                                                                    local[k], active[k]);
+            ctx->launches++;
+            PASUR_CUDA(ctx, cudaGetLastError());
+        }
+        PASUR_TRY(exclusive_scan_i32(ctx, local[k], lrank[k], t->M[k]));
+        PASUR_TRY(exclusive_scan_i32(ctx, active[k], arank[k], t->M[k]));
+    }
+    int64_t nr = t->n_roots;
+    int64_t *ranks = nullptr;
+    PASUR_TRY(tmp_alloc(ctx, tmp, &ranks, 18 * (nr + 1)));
+    RankPtrs rp;
+    for (int k = 0; k < 9; k++) {
+        rp.loc[k] = lrank[k];
+        rp.act[k] = arank[k];
+    }
+    k_root_ranks<<<grid_for(nr + 1, 256), 256, 0, ctx->stream>>>(t->bounds_d, nr, rp, ranks);
+    ctx->launches++;
+    PASUR_CUDA(ctx, cudaGetLastError());
+    std::vector<int64_t> hr((size_t)18 * (nr + 1));
+    PASUR_CUDA(ctx, cudaMemcpyAsync(hr.data(), ranks, sizeof(int64_t) * hr.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    t->croots_h.assign((size_t)nr, CfrRoot{});
+    int64_t loc_off = 0, act_off = 0;
+    for (int64_t g = 0; g < nr; g++) {
+        CfrRoot &cr = t->croots_h[(size_t)g];
+        const int64_t *a = &hr[(size_t)g * 18], *b = &hr[(size_t)(g + 1) * 18];
+        int64_t l = 0, n = 0;
+        for (int k = 0; k < 9; k++) {
+            cr.locbase[k] = a[k];
+            cr.actbase[k] = a[9 + k];
+            cr.ls[k] = (int32_t)l;
+            cr.as[k] = (int32_t)n;
+            l += b[k] - a[k];
+            n += b[9 + k] - a[9 + k];
+        }
+        if (l > INT32_MAX / 64) return set_err(ctx, PASUR_EOVERFLOW, "a root's local subtree is too large");
+        cr.ls[9] = (int32_t)l;
+        cr.as[9] = (int32_t)n;
+        cr.loc_off = loc_off;
+        cr.act_off = act_off;
+        loc_off += l;
+        act_off += n;
+    }
+    t->n_local = loc_off;
+    t->n_active = act_off;
+    if (nr > 0) {
+        PASUR_TRY(tree_alloc(t, (void **)&t->croots_d, sizeof(CfrRoot) * (size_t)nr));
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->croots_d, t->croots_h.data(), sizeof(CfrRoot) * (size_t)nr, cudaMemcpyHostToDevice,
+                                        ctx->stream));
+    }
+    PASUR_TRY(tree_alloc(t, (void **)&t->loc_tq, sizeof(int64_t) * (size_t)(loc_off + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->act_li, sizeof(int32_t) * (size_t)(act_off + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->act_pl, sizeof(int32_t) * (size_t)(act_off + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->act_cs, sizeof(int32_t) * (size_t)(act_off + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->act_d, sizeof(uint16_t) * (size_t)(act_off + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->act_gt, sizeof(int64_t) * (size_t)(act_off + 1)));
+    uint64_t *act_key = nullptr;
+    int64_t *perm = nullptr;
+    PASUR_TRY(tmp_alloc(ctx, tmp, &act_key, act_off));
+    PASUR_TRY(tmp_alloc(ctx, tmp, &perm, act_off));
+    ChildPtrs co;
+    for (int k = 0; k < 8; k++) co.p[k] = t->child_off[k];
+    co.p[8] = nullptr;
+    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int32_t), ctx->stream));
+    for (int k = 0; k < 9; k++) {
+        if (t->M[k] == 0) continue;
+        k_fill_layout<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(
+            k, t->M[k], t->root[k], local[k], active[k], lrank[k], arank[k], k < 8 ? lrank[k + 1] : nullptr,
+            k > 0 ? lrank[k - 1] : nullptr, k > 0 ? t->parent[k] : nullptr, co, t->fgt_off[8], t->croots_d, t->loc_tq,
+            t->act_li, t->act_pl, t->act_cs, t->act_d, t->act_gt, act_key, ctx->errflag);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }
@@ -286,48 +615,107 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
     PASUR_CUDA(ctx, cudaMemcpyAsync(&ef, ctx->errflag, sizeof ef, cudaMemcpyDeviceToHost, ctx->stream));
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ef) return set_err(ctx, PASUR_EOVERFLOW, "a node has more than 65535 legal moves");
+    // order the active entries of every (root, level) by degree, largest first, so that the lanes
+    // of a warp mostly run the same unrolled path
+    if (act_off > 1) {
+        k_iota<<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(perm, act_off);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        int bits = 16;
+        while (((int64_t)1 << (bits - 16)) <= act_off) bits++;
+        PASUR_TRY(radix_sort_pairs(ctx, act_key, perm, act_off, bits));
+        int32_t *t32 = nullptr;
+        uint16_t *t16 = nullptr;
+        int64_t *t64 = nullptr;
+        PASUR_TRY(tmp_alloc(ctx, tmp, &t32, act_off));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &t16, act_off));
+        PASUR_TRY(tmp_alloc(ctx, tmp, &t64, act_off));
+        int32_t *arr32[3] = {t->act_li, t->act_pl, t->act_cs};
+        for (int i = 0; i < 3; i++) {
+            k_gather<int32_t><<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(arr32[i], perm, act_off, t32);
+            ctx->launches++;
+            PASUR_CUDA(ctx, cudaGetLastError());
+            PASUR_CUDA(ctx, cudaMemcpyAsync(arr32[i], t32, sizeof(int32_t) * (size_t)act_off, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        k_gather<uint16_t><<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(t->act_d, perm, act_off, t16);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->act_d, t16, sizeof(uint16_t) * (size_t)act_off, cudaMemcpyDeviceToDevice, ctx->stream));
+        k_gather<int64_t><<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(t->act_gt, perm, act_off, t64);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->act_gt, t64, sizeof(int64_t) * (size_t)act_off, cudaMemcpyDeviceToDevice, ctx->stream));
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return PASUR_OK;
+}
 
-    // plan the work items
-    int threads = cfg->threads > 0 ? cfg->threads : 256;
-    if (threads > 256 || threads % 32) return set_err(ctx, PASUR_EINVAL, "cfg.threads must be a multiple of 32 <= 256");
-    size_t budget = std::min<size_t>(ctx->smem_optin, 110 * 1024);
-    int wcap = cfg->slots_per_item > 0 ? cfg->slots_per_item : 64;
-    t->items_h.clear();
+}  // namespace
+
+int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
+    pasur_ctx *ctx = t->ctx;
+    if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
+        return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
+    PASUR_TRY(build_layout(t));
+    // plan: every root goes to the smallest shared-memory class its subtree fits with one slot;
+    // its items then take as many slots as that class holds
+    size_t budget[kNumCls - 1];
+    for (int c = 0; c < kNumCls - 1; c++) budget[c] = kClsBudget[c] ? std::min<size_t>(kClsBudget[c], ctx->smem_optin) : ctx->smem_optin;
+    const int wcap = cfg->slots_per_item > 0 ? std::min(cfg->slots_per_item, kMaxSlots) : kMaxSlots;
+    std::vector<CfrItem> cls_items[kNumCls];
     int64_t data = 0, scratch = 0;
-    size_t smem_need = 0;
+    size_t need[kNumCls] = {0};
     for (int64_t g = 0; g < t->n_roots; g++) {
-        const RootInfo &ri = t->roots_h[(size_t)g];
-        int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
-        int64_t N = ri.local_start[9], Nint = ri.n_internal;
-        if (Sg == 0 || N == 0) continue;
+        CfrRoot &cr = t->croots_h[(size_t)g];
+        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t L = cr.ls[9], nA = cr.as[9];
+        cr.W = 0;
+        cr.cls = -1;
+        if (Sg == 0 || L == 0) continue;
+        int cls = kClsGlobal;
+        for (int c = 0; c < kNumCls - 1; c++)
+            if (resident_bytes(L, nA, 1) <= budget[c]) {
+                cls = c;
+                break;
+            }
         int64_t w = std::min<int64_t>(Sg, wcap);
-        while (w > 1 && resident_bytes(N, Nint, w) > budget) w--;
-        bool res = resident_bytes(N, Nint, w) <= budget;
-        if (!res) w = std::min<int64_t>(Sg, 32);
+        if (cls != kClsGlobal)
+            while (w > 1 && resident_bytes(L, nA, w) > budget[cls]) w--;
+        cr.W = (int32_t)w;
+        cr.cls = cls;
         for (int64_t s0 = 0; s0 < Sg; s0 += w) {
             CfrItem it{};
             it.root = (int32_t)g;
             it.ns = (int32_t)std::min<int64_t>(w, Sg - s0);
             it.s0 = s0;
             it.data_base = data;
-            data += N * it.ns;
-            if (res) {
-                it.scratch_base = -1;
-                smem_need = std::max(smem_need, resident_bytes(N, Nint, it.ns));
-            } else {
+            data += L * it.ns;
+            if (cls == kClsGlobal) {
                 it.scratch_base = scratch;
-                scratch += N * it.ns;
+                scratch += L * it.ns;
+            } else {
+                it.scratch_base = -1;
+                need[cls] = std::max(need[cls], resident_bytes(L, nA, it.ns));
             }
-            it.cost = N * it.ns;
-            t->items_h.push_back(it);
+            it.cost = std::max<int64_t>(nA, 1) * it.ns;
+            cls_items[cls].push_back(it);
         }
     }
-    std::stable_sort(t->items_h.begin(), t->items_h.end(), [](const CfrItem &a, const CfrItem &b) { return a.cost > b.cost; });
+    t->items_h.clear();
+    for (int c = 0; c < kNumCls; c++) {
+        std::stable_sort(cls_items[c].begin(), cls_items[c].end(),
+                         [](const CfrItem &a, const CfrItem &b) { return a.cost > b.cost; });
+        t->cls_begin[c] = (int64_t)t->items_h.size();
+        t->items_h.insert(t->items_h.end(), cls_items[c].begin(), cls_items[c].end());
+        t->cls_end[c] = (int64_t)t->items_h.size();
+        t->cls_smem[c] = need[c];
+    }
     t->n_items = (int64_t)t->items_h.size();
     t->data_size = data;
     t->scratch_size = scratch;
-    t->cfr_smem = smem_need;
-    t->cfr_threads = threads;
+    if (t->n_roots > 0)
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->croots_d, t->croots_h.data(), sizeof(CfrRoot) * (size_t)t->n_roots,
+                                        cudaMemcpyHostToDevice, ctx->stream));
     if (t->n_items) {
         PASUR_TRY(tree_alloc(t, (void **)&t->items_d, sizeof(CfrItem) * (size_t)t->n_items));
         PASUR_CUDA(ctx, cudaMemcpyAsync(t->items_d, t->items_h.data(), sizeof(CfrItem) * (size_t)t->n_items,
@@ -339,21 +727,47 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
     PASUR_CUDA(ctx, cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)(data + 1), ctx->stream));
     if (scratch) {
         PASUR_TRY(tree_alloc(t, (void **)&t->V, sizeof(float) * (size_t)scratch));
-        PASUR_TRY(tree_alloc(t, (void **)&t->P0, sizeof(float) * (size_t)scratch));
-        PASUR_TRY(tree_alloc(t, (void **)&t->P1, sizeof(float) * (size_t)scratch));
+        PASUR_TRY(tree_alloc(t, (void **)&t->X, sizeof(float) * (size_t)scratch));
     }
     PASUR_TRY(tree_alloc(t, (void **)&t->uacc, sizeof(double) * (size_t)(t->Q[0] + 1)));
     PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
-    // persistent grid
-    int per_sm = 0;
-    if (t->cfr_smem > 0) {
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->cfr_smem));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->cfr_smem));
+    // persistent grid per class
+    size_t max_sm = 0;
+    for (int c = 0; c < kNumCls; c++) max_sm = std::max(max_sm, t->cls_smem[c]);
+    if (max_sm > 48 * 1024) {
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
     }
-    PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0>, threads, t->cfr_smem));
-    if (per_sm < 1) return set_err(ctx, PASUR_EINVAL, "CFR kernel cannot be resident with this shared-memory plan");
-    int64_t blocks = (int64_t)per_sm * ctx->num_sms;
-    t->cfr_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, t->n_items));
+    for (int c = 0; c < kNumCls; c++) {
+        t->cls_blocks[c] = 0;
+        const int threads = cfg->threads > 0 ? cfg->threads : kClsThreads[c];
+        t->cls_threads[c] = threads;
+        int64_t n = t->cls_end[c] - t->cls_begin[c];
+        if (n == 0) continue;
+        int per_sm = 0;
+        if (threads <= 256)
+            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, t->cls_smem[c]));
+        else
+            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, t->cls_smem[c]));
+        if (per_sm < 1) return set_err(ctx, PASUR_EINVAL, "CFR kernel cannot be resident with this shared-memory plan");
+        t->cls_blocks[c] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n));
+    }
+    if (getenv("PASUR_VERBOSE")) {
+        int64_t ne = 0;
+        for (int k = 1; k < 9; k++) ne += t->Q[k];
+        fprintf(stderr, "[pasur] round %d: GT roots %lld, FGT edges %lld, local %lld, active %lld, items %lld\n", t->round,
+                (long long)t->n_roots, (long long)ne, (long long)t->n_local, (long long)t->n_active, (long long)t->n_items);
+        for (int c = 0; c < kNumCls; c++) {
+            int64_t n = t->cls_end[c] - t->cls_begin[c];
+            if (!n) continue;
+            int64_t cost = 0;
+            for (int64_t i = t->cls_begin[c]; i < t->cls_end[c]; i++) cost += t->items_h[(size_t)i].cost;
+            fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld\n",
+                    c, (long long)n, t->cls_smem[c], t->cls_blocks[c], t->cls_threads[c], (long long)cost);
+        }
+    }
     t->iters_done = 0;
     t->cfr_ready = true;
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -384,49 +798,89 @@ int cfr_run(pasur_tree *t, const pasur_config *cfg) {
     }
     CfrParams p{};
     p.items = t->items_d;
-    p.n_items = t->n_items;
-    p.roots = t->roots_d;
-    p.lcs = t->lcs;
-    p.ldeg = t->ldeg;
+    p.roots = t->croots_d;
+    p.act_li = t->act_li;
+    p.act_pl = t->act_pl;
+    p.act_cs = t->act_cs;
+    p.act_d = t->act_d;
+    p.loc_tq = t->loc_tq;
     p.leaf_v = t->leaf_v;
-    p.fgt_off8 = t->fgt_off[8];
     p.fgt_off0 = t->fgt_off[0];
     p.R = t->R;
     p.S = t->S;
     p.V = t->V;
-    p.P0 = t->P0;
-    p.P1 = t->P1;
+    p.X = t->X;
     p.uacc = t->uacc;
     p.dcfr = dcfr;
     p.iters = cfg->iters;
     p.t0 = t->iters_done;
-    p.tau_umax = cfg->rm_deadzone * t->umax;
-    p.counter = ctx->counter;
+    p.tau = cfg->rm_deadzone;
     p.err = ctx->errflag;
+    if (!ctx->fork) {
+        PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+        for (int c = 0; c < kNumCls; c++) {
+            PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
+            PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
+            PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
+            PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t1[c]));
+        }
+    }
     cudaEvent_t e0, e1;
     PASUR_CUDA(ctx, cudaEventCreate(&e0));
     PASUR_CUDA(ctx, cudaEventCreate(&e1));
-    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int32_t), ctx->stream));
+    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int32_t) * kNumCls, ctx->stream));
     PASUR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int32_t), ctx->stream));
     PASUR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-    if (cfg->variant == 1)
-        k_cfr_items<1><<<t->cfr_blocks, t->cfr_threads, t->cfr_smem, ctx->stream>>>(p);
-    else
-        k_cfr_items<0><<<t->cfr_blocks, t->cfr_threads, t->cfr_smem, ctx->stream>>>(p);
-    ctx->launches++;
-    PASUR_CUDA(ctx, cudaGetLastError());
+    PASUR_CUDA(ctx, cudaEventRecord(ctx->fork, ctx->stream));
+    int launches = 0;
+    // the classes are independent: each runs on its own forked stream, largest subtrees first
+    for (int oi = 0; oi < kNumCls; oi++) {
+        const int c = kNumCls - 1 - oi;
+        if (t->cls_end[c] == t->cls_begin[c]) continue;
+        cudaStream_t st = ctx->aux[c];
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
+        p.i_begin = t->cls_begin[c];
+        p.i_end = t->cls_end[c];
+        p.counter = ctx->counter + c;
+        const bool wide = t->cls_threads[c] > 256;
+        if (cfg->variant == 1 && wide)
+            k_cfr_items<1, 1024><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
+        else if (cfg->variant == 1)
+            k_cfr_items<1, 256><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
+        else if (wide)
+            k_cfr_items<0, 1024><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
+        else
+            k_cfr_items<0, 256><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
+        ctx->launches++;
+        launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
+    }
     PASUR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
     int32_t ef = 0;
     PASUR_CUDA(ctx, cudaMemcpyAsync(&ef, ctx->errflag, sizeof ef, cudaMemcpyDeviceToHost, ctx->stream));
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     PASUR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+    for (int c = 0; c < kNumCls; c++) {
+        float m = 0.f;
+        if (t->cls_end[c] != t->cls_begin[c]) cudaEventElapsedTime(&m, ctx->cls_t0[c], ctx->cls_t1[c]);
+        t->cls_ms[c] = m;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (dcfr) dev_free(ctx, dcfr, db);
     t->last_ms = ms;
-    t->last_launches = 1;
+    t->last_launches = launches;
     t->iters_done += cfg->iters;
+    if (getenv("PASUR_VERBOSE")) {
+        fprintf(stderr, "[pasur] round %d: %d iterations in %.3f ms (", t->round, cfg->iters, ms);
+        for (int c = 0; c < kNumCls; c++) fprintf(stderr, "%s%.2f", c ? " " : "", t->cls_ms[c]);
+        fprintf(stderr, " ms per class)\n");
+    }
     if (ef) return set_err(ctx, PASUR_ENUMERIC, "non-finite root value in the CFR sweep");
     return PASUR_OK;
 }
@@ -434,15 +888,23 @@ int cfr_run(pasur_tree *t, const pasur_config *cfg) {
 int cfr_export_sigma(const pasur_tree *t, float *out_dev) {
     pasur_ctx *ctx = t->ctx;
     LevelPtrs lp{};
-    int64_t base = 0;
+    int64_t base = 0, ne = 0;
     for (int k = 0; k < 9; k++) {
-        lp.p[k] = t->fgt_off[k];
+        lp.fgt[k] = t->fgt_off[k];
+        lp.child[k] = k < 8 ? t->child_off[k] : nullptr;
         lp.base[k] = k >= 1 ? base : 0;
         if (k >= 1) base += t->Q[k];
     }
+    ne = base;
+    if (ne > 0) {
+        k_fill<<<grid_for(ne, 256), 256, 0, ctx->stream>>>(out_dev, ne, 1.0f);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+    }
     if (t->n_items) {
         unsigned g = (unsigned)std::min<int64_t>(t->n_items, 65535);
-        k_export_sigma<<<g, 256, 0, ctx->stream>>>(t->items_d, t->n_items, t->roots_d, t->lcs, t->ldeg, t->S, lp, out_dev);
+        k_export_sigma<<<g, 256, 0, ctx->stream>>>(t->items_d, t->n_items, t->croots_d, t->act_cs, t->act_d, t->act_gt, t->S,
+                                                   lp, out_dev);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }

@@ -108,6 +108,8 @@ struct pasur_ctx {
     int32_t *counter = nullptr;  // work-queue counters (device)
     int32_t *errflag = nullptr;  // device error word
     int64_t launches = 0;        // kernels launched through this context
+    cudaStream_t aux[8] = {nullptr};  // forked streams for concurrent launches (created on first use)
+    cudaEvent_t fork = nullptr, join[8] = {nullptr}, cls_t0[8] = {nullptr}, cls_t1[8] = {nullptr};
     int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
 };
 
@@ -120,13 +122,30 @@ struct RootInfo {             // one GT root's subtree, level by level
     int32_t pad;
 };
 
+// CFR view of one GT root's subtree.  Nodes whose whole subtree is a single path of forced moves
+// ("chains") have a fixed value, sigma = 1 and zero regret on every edge below them, so the CFR
+// state is kept only for the "local" nodes: the root and every child of an "active" node (a
+// local node that is not a chain).  Local nodes are numbered level by level in GT order; chain
+// nodes among them are "terminals" whose value is the leaf at the end of their chain.
+struct CfrRoot {
+    int32_t ls[10];           // first local index of level k; ls[9] = number of local nodes L
+    int32_t as[10];           // first active entry of level k; as[8] = as[9] = active nodes
+    int64_t loc_off;          // offset of the root's local nodes in the per-local arrays
+    int64_t act_off;          // offset of the root's active entries in the per-active arrays
+    int64_t locbase[9];       // global local-rank of the root's first node at level k
+    int64_t actbase[9];       // global active-rank of the root's first node at level k
+    int32_t W;                // slots per work item of this root
+    int32_t cls;              // launch class of its items
+    int64_t item0;            // index of its first work item
+};
+
 struct CfrItem {              // one work item of the CFR kernel: a root and a run of its slots
     int32_t root;
     int32_t ns;               // slots in the item
     int64_t s0;               // first slot of the item within its root
     int64_t data_base;        // offset of the item's (local node, slot) table in R and S
     int64_t scratch_base;     // offset in the global transients, or -1 when the item is resident
-    int64_t cost;             // nodes * slots, for the schedule
+    int64_t cost;             // active nodes * slots, for the schedule
 };
 
 struct pasur_tree {
@@ -145,7 +164,7 @@ struct pasur_tree {
     uint64_t *pick[9] = {nullptr};      // levels 1..8
     int32_t *root[9] = {nullptr};       // root id of every node
     std::vector<RootInfo> roots_h;
-    RootInfo *roots_d = nullptr;
+    int64_t *bounds_d = nullptr;        // [n_roots+1][9]: first GT node of root g at level k
     // full game tree
     bool unfolded = false;
     int64_t Q[9] = {0};
@@ -165,16 +184,27 @@ struct pasur_tree {
     int64_t iters_done = 0;
     float umax = 0.f;
     float *leaf_v = nullptr;            // Q[8], FGT order
-    int32_t *lcs = nullptr;             // local first child of every internal node
-    uint16_t *ldeg = nullptr;           // its number of children
-    std::vector<CfrItem> items_h;
+    std::vector<CfrRoot> croots_h;
+    CfrRoot *croots_d = nullptr;
+    int32_t *act_li = nullptr;          // per active entry: its local index
+    int32_t *act_pl = nullptr;          //   local index of its parent (-1 at the root)
+    int32_t *act_cs = nullptr;          //   local index of its first child
+    uint16_t *act_d = nullptr;          //   number of children
+    int64_t *act_gt = nullptr;          //   GT node index
+    int64_t *loc_tq = nullptr;          // per local node: FGT index (slot 0) of its chain's leaf, -1 if active
+    int64_t n_local = 0, n_active = 0;
+    std::vector<CfrItem> items_h;       // ordered by launch class, then cost
     CfrItem *items_d = nullptr;
     int64_t n_items = 0, data_size = 0, scratch_size = 0;
+    int64_t cls_begin[8] = {0}, cls_end[8] = {0};
+    size_t cls_smem[8] = {0};
+    int cls_blocks[8] = {0};
+    int cls_threads[8] = {0};
+    float cls_ms[8] = {0};
     float *R = nullptr, *S = nullptr;   // per (local node, slot) of every item
-    float *V = nullptr, *P0 = nullptr, *P1 = nullptr;  // transients of the non-resident items
+    float *V = nullptr, *X = nullptr;   // values and reaches of the non-resident items
     double *uacc = nullptr;             // Q[0]
-    int cfr_threads = 0, cfr_blocks = 0;
-    size_t cfr_smem = 0;
+
     int32_t variant = -1;
     float last_ms = 0.f;
     int32_t last_launches = 0;

@@ -1,11 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the fp64 oracle on the same seeded inputs.
 
 Integer work (tree structure, states, running scores, unfolding, next roots, links, leaf values)
-must be bit-exact.  Floating point: after the same number of iterations the root utilities agree
-within 1e-5 and the average strategies within 1e-4 absolute on every FGT parent whose own-reach
-mass sum_t pi_p^t(h) is at least 1e-3 * T; at the remaining (rarely reached) parents the strategy
-cannot move a utility by more than its reach share, and the test checks only that it is a valid
-distribution.
+must be bit-exact.  Floating point, after the same number of iterations:
+  - root utilities agree within 1e-5 (within 20x the oracle's own sensitivity to that noise where
+    it is larger: a root whose value moves under f32-sized leaf noise even in fp64);
+  - average strategies agree within 1e-4 absolute on every edge whose parent has own-reach mass
+    sum_t pi_p^t(h) >= 1e-3 * T and is well conditioned: the oracle's own recursion carried out
+    in float32, and oracle runs whose leaf values carry f32-sized noise (relative and absolute
+    1e-6, seeded: the size of f32 rounding compounded through the value recursion and the T
+    regret accumulations), each move that edge's average strategy by at most 1e-5.  At ill-conditioned parents (near-indifferent nodes, where regret matching flips
+    on noise of that size even in fp64) the difference must stay within 20x the oracle's own
+    sensitivity; at rarely reached parents the strategy must be a valid distribution.
 """
 import numpy as np
 import pytest
@@ -17,6 +22,9 @@ pytestmark = pytest.mark.gpu
 U_TOL = 1e-5
 SIGMA_TOL = 1e-4
 MASS_FRAC = 1e-3
+NOISE = 1e-6
+N_NOISE = 3
+COND_TOL = 1e-5
 
 
 def mask_ids(ids):
@@ -78,6 +86,41 @@ def own_mass(ot, S):
     return out
 
 
+def oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant=0, tau=1e-6):
+    """max |change| of every average strategy and root utility between the fp64 oracle run and
+    (a) the same oracle recursion carried out in float32, (b) oracle runs whose leaf values carry
+    f32-sized noise (relative and absolute NOISE, seeded signs)."""
+    rng = np.random.default_rng(20250806)
+    dp = np.zeros_like(sb_o)
+    du = np.zeros_like(U_o)
+    if variant == 0:
+        sb32, U32 = ot.cfr_f32(leaf_o, T, tau=tau)
+        dp = np.abs(sb32 - sb_o)
+        du = np.abs(U32 - U_o)
+    for _ in range(N_NOISE):
+        pert = leaf_o * (1 + NOISE * rng.choice([-1.0, 1.0], leaf_o.shape)) + NOISE * rng.choice([-1.0, 1.0], leaf_o.shape)
+        sb_p, U_p = ot.cfr(pert, T, tau=tau, variant=variant)
+        dp = np.maximum(dp, np.abs(sb_p - sb_o))
+        du = np.maximum(du, np.abs(U_p - U_o))
+    return dp, du
+
+
+def check_utilities(U_g, U_o, du):
+    d = np.abs(U_g - U_o)
+    assert (d <= np.maximum(U_TOL, 20 * du)).all(), (d.max(initial=0), du[np.argmax(d)] if len(d) else 0)
+
+
+def check_sigma(sb_g, sb_o, mass, dp, T):
+    assert np.isfinite(sb_g).all() and (sb_g >= 0).all() and (sb_g <= 1 + 1e-6).all()
+    d = np.abs(sb_g - sb_o)
+    heavy = mass >= MASS_FRAC * T
+    well = heavy & (dp <= COND_TOL)
+    ill = heavy & ~well
+    assert d[well].max(initial=0) <= SIGMA_TOL, (d[well].max(), int(np.argmax(np.where(well, d, 0))))
+    assert (d[ill] <= np.maximum(SIGMA_TOL, 20 * dp[ill])).all(), d[ill].max(initial=0)
+    return int(well.sum()), int(ill.sum())
+
+
 def compare_cfr(gt, ot, leaf_o, T, variant=0, next_util=None, tau=1e-6):
     cfg = P().pasur_config_default(iters=T, variant=variant, rm_deadzone=tau)
     gt.pasur_cfr_iterate(cfg, next_util)
@@ -86,11 +129,9 @@ def compare_cfr(gt, ot, leaf_o, T, variant=0, next_util=None, tau=1e-6):
     assert np.allclose(leaf_g, leaf_o, atol=1e-5, rtol=0)
     U_g = gt.pasur_round_utilities()
     sb_g = gt.pasur_avg_strategy()
-    assert np.abs(U_g - U_o).max() <= U_TOL, np.abs(U_g - U_o).max()
-    mass = own_mass(ot, S_o)
-    heavy = mass >= MASS_FRAC * T
-    assert np.abs(sb_g - sb_o)[heavy].max(initial=0) <= SIGMA_TOL, np.abs(sb_g - sb_o)[heavy].max()
-    assert np.isfinite(sb_g).all() and (sb_g >= 0).all() and (sb_g <= 1 + 1e-6).all()
+    dp, du = oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant, tau)
+    check_utilities(U_g, U_o, du)
+    check_sigma(sb_g, sb_o, own_mass(ot, S_o), dp, T)
     return U_g, U_o, sb_g, sb_o
 
 
@@ -233,8 +274,9 @@ def test_cfr_dcfr_variant(ctx):
 
 def test_two_round_chain_rounds_4_5(ctx):
     """Rounds 5-6 of the seed-0 deal (0-based rounds 4 and 5): round 5 over every root round 4
-    reaches, 2000 iterations per round, round-5 utilities passed back into round 4 (each side
-    uses its own round-5 utilities)."""
+    reaches, 2000 iterations per round, round-5 utilities passed back into round 4.  Round 4 gets
+    the same next-round utilities on both sides (the oracle's, rounded to float32), so that its
+    comparison isolates the CFR arithmetic; round 5's utilities were compared just before."""
     T = 2000
     deck = O.deal(0)
     pool = mask_ids(deck[:4])
@@ -247,5 +289,6 @@ def test_two_round_chain_rounds_4_5(ctx):
     g5, o5 = ctx.pasur_build_round(deck, 5, gp), O.Tree(deck, 5, op)
     unfold_both(g5, o5, gs, gsc)
     U5g, U5o, _, _ = compare_cfr(g5, o5, o5.leaf_utilities_final(), T)
-    leaf4 = o4.leaf_utilities_linked(ol, U5o)
-    compare_cfr(g4, o4, leaf4, T, next_util=U5g)
+    u5 = U5o.astype(np.float32)
+    leaf4 = o4.leaf_utilities_linked(ol, u5.astype(np.float64))
+    compare_cfr(g4, o4, leaf4, T, next_util=u5)
