@@ -172,6 +172,25 @@ int pasur_leaf_values(const pasur_tree *tree, float *out, int64_t cap);
  * launches), the number of FGT edges, and the kernel launches it made. */
 int pasur_last_cfr_stats(const pasur_tree *tree, float *ms, int64_t *edges, int32_t *launches);
 
+/* Exclusive prefix sum of per-node move counts into CSR child offsets, allocating nothing.
+ * This is the step between the count and emit passes of the level expansion; the paper has no
+ * counterpart (its expansion runs on PyTorch tensor ops).  It exists for callers that cannot
+ * allocate device memory at the point of the call: applications that give all GPU memory to their
+ * own arena, plug-ins inside a host program that owns the allocator, code that must not risk an
+ * out-of-memory failure or the allocator's locks mid-run.  pasur_build_round does the same step
+ * with scratch it allocates; this variant uses a fixed 32 KB array compiled into the library
+ * (every GPU that loads the library holds it until the process exits).
+ *   counts   device, n int32 (each >= 0); offsets: device, n+1 int64, offsets[i] = sum of
+ *            counts[0..i), offsets[n] = total.  Both stay owned by the caller.
+ *   n        0 <= n <= 4,194,303, else PASUR_EOVERFLOW (pasur_last_error(NULL) says why).
+ *   cuda_stream  cudaStream_t the work is queued on (NULL = the default stream); the call
+ *            returns without waiting.
+ * The first call made with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls share the
+ * array: two calls that overlap on the GPU (other streams, or other host threads on the same
+ * stream without ordering) race and may return wrong offsets. */
+int pasur_move_offsets_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

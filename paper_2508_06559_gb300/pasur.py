@@ -27,7 +27,7 @@ EXPORTS = [
     "pasur_deal",
     "pasur_build_round", "pasur_tree_free", "pasur_tree_sizes", "pasur_unfold", "pasur_cfr_iterate",
     "pasur_avg_strategy", "pasur_round_utilities", "pasur_next_roots", "pasur_export_level", "pasur_leaf_values",
-    "pasur_last_cfr_stats",
+    "pasur_last_cfr_stats", "pasur_move_offsets_noalloc",
 ]
 
 
@@ -80,6 +80,7 @@ def load() -> C.CDLL:
     L.pasur_export_level.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, vp, vp]
     L.pasur_leaf_values.argtypes = [vp, vp, i64]
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
+    L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     for name in EXPORTS:
         if name != "pasur_last_error":
             getattr(L, name).restype = C.c_int
@@ -118,6 +119,13 @@ def pasur_deal(seed: int) -> np.ndarray:
     deck = np.zeros(52, np.uint8)
     _check(load().pasur_deal(C.c_uint64(seed), _ptr(deck)))
     return deck
+
+
+def pasur_move_offsets_noalloc(counts_dev, offsets_dev, stream=None) -> None:
+    """CSR offsets (n+1 int64, device) from per-node move counts (n int32, device) without any
+    device allocation; see include/pasur.h.  Raises PasurError on failure."""
+    n = counts_dev.numel()
+    _check(load().pasur_move_offsets_noalloc(_ptr(counts_dev), n, _ptr(offsets_dev), stream))
 
 
 def scores_array(rows) -> np.ndarray:
