@@ -33,7 +33,10 @@ WORKLOADS = {
     "full_game": (0, "full six-round game of one seeded deal, round-by-round backward CFR"),
     "rounds_4_5": (4, "rounds 5-6 (0-based 4-5) of one seeded deal, round 5 unfolded over every score round 4 reaches"),
     "final_round": (5, "final round of one seeded deal as a standalone round, score (0,0,0,0)"),
+    "batch64": (3, "64 seeded deals (seeds S..S+63), rounds 4-6 (0-based 3-5) of each from the standalone root, "
+                   "solved together: one merged persistent launch per round and size class under a CUDA graph"),
 }
+BATCH_DEALS = 64
 METRIC = "CFR node-updates/sec"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 ALG_BYTES_PER_UPDATE = 16   # regret and strategy sum, f32, read + write, per node-update
@@ -92,6 +95,36 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
     for t in trees:
         t.free()
     return updates, kms, d2h, h2d, root_u, info
+
+
+def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
+    """One step of the batched workload: build every deal's rounds, solve them in the batch,
+    write out every tree's average strategies and root utilities, free."""
+    cfg = P.pasur_config_default(iters=T)
+    b = P.Batch(ctx, decks, first_round, cfg)
+    u = b.pasur_batch_solve()
+    ms, edges, launches = b.pasur_batch_stats()
+    d2h = 0
+    info = []
+    for d in range(len(decks)):
+        for r in range(first_round, 6):
+            t = b.pasur_batch_tree(d, r)
+            q = t.pasur_tree_sizes()[1]
+            ne = int(q[1:].sum())
+            if out_device:
+                U = torch.empty(int(q[0]), dtype=torch.float32, device="cuda")
+                sb = torch.empty(max(ne, 1), dtype=torch.float32, device="cuda")
+            else:
+                U = np.empty(int(q[0]), np.float32)
+                sb = np.empty(max(ne, 1), np.float32)
+                d2h += U.nbytes + sb.nbytes
+            t.pasur_round_utilities(U)
+            if ne:
+                t.pasur_avg_strategy(sb)
+            if d == 0:
+                info.append(q.tolist())
+    b.free()
+    return edges * T, ms, d2h, decks.nbytes, float(u[0]), info
 
 
 class ClockSampler:
@@ -164,12 +197,18 @@ def run_ours(args, rank, world, dist):
     ctx = P.Ctx(dev, 0, stream.cuda_stream)
     first_round, desc = WORKLOADS[args.workload]
     seed = args.seed + rank
-    deck = P.pasur_deal(seed)
     T = args.iters
+    if args.workload == "batch64":
+        base = args.seed + rank * BATCH_DEALS
+        deck = np.stack([P.pasur_deal(base + i) for i in range(BATCH_DEALS)])
+        solve = solve_batch
+    else:
+        deck = P.pasur_deal(seed)
+        solve = solve_deal
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
-        solve_deal(P, ctx, deck, first_round, T, True, torch)
+        solve(P, ctx, deck, first_round, T, True, torch)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -183,7 +222,7 @@ def run_ours(args, rank, world, dist):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            u, kms, _, _, root_u, info = solve_deal(P, ctx, deck, first_round, T, True, torch)
+            u, kms, _, _, root_u, info = solve(P, ctx, deck, first_round, T, True, torch)
             e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -206,7 +245,7 @@ def run_ours(args, rank, world, dist):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, _, d2h, h2d, _, _ = solve_deal(P, ctx, deck, first_round, T, False, torch)
+        _, _, d2h, h2d, _, _ = solve(P, ctx, deck, first_round, T, False, torch)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     if dist:

@@ -172,6 +172,33 @@ int pasur_leaf_values(const pasur_tree *tree, float *out, int64_t cap);
  * launches), the number of FGT edges, and the kernel launches it made. */
 int pasur_last_cfr_stats(const pasur_tree *tree, float *ms, int64_t *edges, int32_t *launches);
 
+/* ---- batched exact solve of many deals ---------------------------------------------------- */
+typedef struct pasur_batch pasur_batch;
+
+/* Build rounds first_round..5 of n_deals seeded deals (decks: host, 52 bytes per deal), each from
+ * the standalone root of first_round (pool = deck[0:4], score (0,0,0,0)), with every round's
+ * unfolding and links, and plan their CFR: the work items of all deals' trees of one round are
+ * merged into one persistent launch per shared-memory class (largest subtrees first).  With
+ * cfg->threads == 0 an autotuner times candidate block sizes per class on the round with the most
+ * work and keeps the fastest.  cfg is fixed for the batch.  The batch owns its trees. */
+int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const pasur_config *cfg,
+                       pasur_batch **out);
+
+/* Solve the batch from scratch: cfg->iters CFR iterations per round, round 5 first, each round's
+ * leaf values from the next round's average root utilities (eq. passuputil).  The first call
+ * captures the whole backward sweep into a CUDA graph; every call replays it.  root_util_out
+ * (host or device, may be NULL): the average utility of every deal's root of first_round. */
+int pasur_batch_solve(pasur_batch *b, float *root_util_out, int64_t cap);
+
+/* Borrow the tree of (deal, round) for pasur_avg_strategy, pasur_round_utilities, pasur_tree_sizes
+ * and the exports; it stays owned by the batch (do not free it). */
+int pasur_batch_tree(const pasur_batch *b, int64_t deal, int round, pasur_tree **tree_out);
+
+/* Device time of the last pasur_batch_solve (CUDA events around the graph launch), the number of
+ * FGT edges of all trees, and the kernel launches in one solve. */
+int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *launches);
+int pasur_batch_free(pasur_batch *b);
+
 /* Exclusive prefix sum of per-node move counts into CSR child offsets, allocating nothing.
  * This is the step between the count and emit passes of the level expansion; the paper has no
  * counterpart (its expansion runs on PyTorch tensor ops).  It exists for callers that cannot

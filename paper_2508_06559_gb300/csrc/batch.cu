@@ -1,0 +1,306 @@
+// Batched exact solve of many seeded deals: every deal's rounds are built and unfolded up front,
+// the work items of all deals' trees of one round are merged into one plan (one persistent
+// launch per shared-memory class, largest subtrees first across all deals), an autotuner picks
+// the block size of every class on the largest round, and the whole backward sweep (leaf values,
+// CFR, root utilities, round 5 down to the first round) is captured once into a CUDA graph and
+// replayed.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "pasur_internal.cuh"
+
+struct pasur_batch {
+    pasur_ctx *ctx = nullptr;
+    int first_round = 0, n_rounds = 0;
+    int64_t n_deals = 0;
+    std::vector<pasur_tree *> trees;      // [deal * n_rounds + (round - first_round)]
+    std::vector<CfrPlan> plans;           // per round (index round - first_round)
+    std::vector<float *> util;            // per tree: average root utilities (device)
+    std::vector<std::pair<void *, size_t>> owned;
+    pasur_config cfg{};
+    float *dcfr = nullptr;
+    size_t dcfr_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_launches = 0, edges = 0;
+    float last_ms = 0.f;
+    bool solved = false;
+};
+
+namespace pasur {
+namespace {
+
+pasur_tree *tree_of(pasur_batch *b, int64_t d, int ri) { return b->trees[(size_t)(d * b->n_rounds + ri)]; }
+
+void free_batch(pasur_batch *b) {
+    pasur_ctx *ctx = b->ctx;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &o : b->owned) dev_free(ctx, o.first, o.second);
+    b->owned.clear();
+    for (pasur_tree *t : b->trees)
+        if (t) pasur_tree_free(t);
+    b->trees.clear();
+    cudaStreamSynchronize(ctx->stream);
+}
+
+int batch_alloc(pasur_batch *b, void **p, size_t bytes) {
+    PASUR_TRY(dev_alloc(b->ctx, p, bytes));
+    b->owned.push_back({*p, bytes});
+    return PASUR_OK;
+}
+
+// Time one class of a plan alone for a few iterations at each candidate block size; keep the best.
+int autotune(pasur_batch *b, CfrPlan &plan) {
+    pasur_ctx *ctx = b->ctx;
+    pasur_config cfg = b->cfg;
+    cfg.iters = 4;
+    cudaEvent_t e0, e1;
+    PASUR_CUDA(ctx, cudaEventCreate(&e0));
+    PASUR_CUDA(ctx, cudaEventCreate(&e1));
+    for (int c = 0; c < 8; c++) {
+        if (plan.cls_end[c] == plan.cls_begin[c]) continue;
+        const int def = plan.cls_threads[c];
+        const int cand_small[3] = {64, 128, 256}, cand_wide[3] = {256, 512, 1024};
+        const int *cand = def > 256 ? cand_wide : cand_small;
+        CfrPlan one = plan;
+        for (int o = 0; o < 8; o++)
+            if (o != c) one.cls_begin[o] = one.cls_end[o] = 0;
+        float best_ms = 1e30f;
+        int best = def;
+        for (int i = 0; i < 3; i++) {
+            int blocks = 0;
+            PASUR_TRY(cfr_occupancy(ctx, cand[i], one.cls_smem[c], one.cls_end[c] - one.cls_begin[c], &blocks));
+            if (blocks <= 0) continue;
+            one.cls_threads[c] = cand[i];
+            one.cls_blocks[c] = blocks;
+            PASUR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+            PASUR_TRY(cfr_launch_plan(ctx, one, &cfg, 0, nullptr));
+            PASUR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+            PASUR_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PASUR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand[i];
+            }
+        }
+        // apply to every round's plan
+        for (CfrPlan &pl : b->plans) {
+            if (pl.cls_end[c] == pl.cls_begin[c]) continue;
+            int blocks = 0;
+            PASUR_TRY(cfr_occupancy(ctx, best, pl.cls_smem[c], pl.cls_end[c] - pl.cls_begin[c], &blocks));
+            if (blocks > 0) {
+                pl.cls_threads[c] = best;
+                pl.cls_blocks[c] = blocks;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return PASUR_OK;
+}
+
+// one backward sweep on ctx->stream without host synchronisation (captured into the graph)
+int record_sweep(pasur_batch *b) {
+    pasur_ctx *ctx = b->ctx;
+    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int32_t), ctx->stream));
+    for (int ri = b->n_rounds - 1; ri >= 0; ri--) {
+        for (int64_t d = 0; d < b->n_deals; d++) {
+            pasur_tree *t = tree_of(b, d, ri);
+            PASUR_CUDA(ctx, cudaMemsetAsync(t->R, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
+            PASUR_CUDA(ctx, cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
+            PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
+            const float *next = ri + 1 < b->n_rounds ? b->util[(size_t)(d * b->n_rounds + ri + 1)] : nullptr;
+            PASUR_TRY(launch_leaf_values(t, next, nullptr));
+        }
+        PASUR_TRY(cfr_launch_plan(ctx, b->plans[(size_t)ri], &b->cfg, 0, b->dcfr));
+        for (int64_t d = 0; d < b->n_deals; d++)
+            PASUR_TRY(cfr_export_utilities_n(tree_of(b, d, ri), b->cfg.iters, b->util[(size_t)(d * b->n_rounds + ri)]));
+    }
+    return PASUR_OK;
+}
+
+}  // namespace
+}  // namespace pasur
+
+using namespace pasur;
+
+extern "C" {
+
+int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const pasur_config *cfg,
+                       pasur_batch **out) {
+    if (!ctx || !out || !cfg || (n_deals > 0 && !decks)) return ctx ? set_err(ctx, PASUR_EINVAL, "pasur_batch_create: NULL argument") : PASUR_EINVAL;
+    *out = nullptr;
+    if (n_deals < 1 || n_deals > (1 << 20)) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: n_deals must be 1..2^20");
+    if (first_round < 0 || first_round > 5) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: first_round must be 0..5");
+    if (cfg->iters < 1 || (cfg->variant != 0 && cfg->variant != 1))
+        return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: cfg.iters >= 1 and variant 0 or 1 required");
+    cudaSetDevice(ctx->device);
+    pasur_batch *b = new pasur_batch();
+    b->ctx = ctx;
+    b->first_round = first_round;
+    b->n_rounds = 6 - first_round;
+    b->n_deals = n_deals;
+    b->cfg = *cfg;
+    b->trees.assign((size_t)(n_deals * b->n_rounds), nullptr);
+    b->util.assign(b->trees.size(), nullptr);
+    int rc = PASUR_OK;
+    // forward: every deal's rounds from the standalone convention root (pool deck[0:4], score 0)
+    for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
+        const uint8_t *deck = decks + 52 * d;
+        uint64_t pool0 = 0;
+        for (int i = 0; i < 4; i++) pool0 |= 1ULL << deck[i];
+        std::vector<uint64_t> pools(1, pool0);
+        std::vector<int64_t> soff = {0, 1};
+        std::vector<pasur_score> scores(1, pasur_score{0, 0, 0, 0});
+        for (int ri = 0; ri < b->n_rounds && rc == PASUR_OK; ri++) {
+            pasur_tree *t = nullptr;
+            rc = pasur_build_round(ctx, deck, first_round + ri, pools.data(), (int64_t)pools.size(), &t);
+            if (rc != PASUR_OK) break;
+            b->trees[(size_t)(d * b->n_rounds + ri)] = t;
+            rc = pasur_unfold(t, soff.data(), scores.data(), nullptr);
+            if (rc == PASUR_OK) rc = tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(t->Q[8] + 1));
+            if (rc == PASUR_OK) rc = tree_alloc(t, (void **)&b->util[(size_t)(d * b->n_rounds + ri)], sizeof(float) * (size_t)(t->Q[0] + 1));
+            if (rc == PASUR_OK && t->M[8] > 0)
+                rc = cudaMemsetAsync(t->leaf_v, 0, sizeof(float) * (size_t)(t->Q[8] + 1), ctx->stream) == cudaSuccess ? PASUR_OK : PASUR_ECUDA;
+            if (rc == PASUR_OK && first_round + ri < 5) {
+                int64_t np = 0, nr = 0;
+                rc = pasur_next_roots(t, nullptr, 0, nullptr, nullptr, 0, nullptr, &np, &nr);
+                if (rc == PASUR_OK) {
+                    pools.assign((size_t)np, 0);
+                    soff.assign((size_t)np + 1, 0);
+                    scores.assign((size_t)nr, pasur_score{});
+                    rc = pasur_next_roots(t, pools.data(), np, soff.data(), scores.data(), nr, nullptr, &np, &nr);
+                }
+            }
+        }
+    }
+    // CFR layouts and one merged plan per round
+    b->plans.resize((size_t)b->n_rounds);
+    for (int ri = 0; ri < b->n_rounds && rc == PASUR_OK; ri++) {
+        std::vector<CfrItem> cls_items[8];
+        size_t need[8] = {0};
+        std::vector<TreeView> views;
+        for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
+            pasur_tree *t = tree_of(b, d, ri);
+            std::vector<CfrItem> own[8];
+            rc = cfr_setup_tree(t, cfg, (int)d, own, need);
+            if (rc != PASUR_OK) break;
+            t->cfr_ready = true;
+            t->variant = cfg->variant;
+            // the tree keeps its own items for exporting its average strategy
+            t->plan.items_h.clear();
+            for (int c = 0; c < 8; c++) {
+                t->plan.items_h.insert(t->plan.items_h.end(), own[c].begin(), own[c].end());
+                cls_items[c].insert(cls_items[c].end(), own[c].begin(), own[c].end());
+            }
+            t->plan.n_items = (int64_t)t->plan.items_h.size();
+            if (t->plan.n_items) {
+                rc = tree_alloc(t, (void **)&t->plan.items_d, sizeof(CfrItem) * (size_t)t->plan.n_items);
+                if (rc == PASUR_OK &&
+                    cudaMemcpyAsync(t->plan.items_d, t->plan.items_h.data(), sizeof(CfrItem) * (size_t)t->plan.n_items,
+                                    cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+                    rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_create: copy items");
+            }
+            views.push_back(t->view);
+            b->edges += t->Q[1] + t->Q[2] + t->Q[3] + t->Q[4] + t->Q[5] + t->Q[6] + t->Q[7] + t->Q[8];
+        }
+        if (rc == PASUR_OK) rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned);
+    }
+    if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
+    if (rc == PASUR_OK && b->dcfr) b->owned.push_back({b->dcfr, b->dcfr_bytes});
+    if (rc == PASUR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_create: sync");
+    // autotune the block size of every class on the round with the most work
+    if (rc == PASUR_OK && cfg->threads == 0) {
+        int big = 0;
+        int64_t best = -1;
+        for (int ri = 0; ri < b->n_rounds; ri++) {
+            int64_t cost = 0;
+            for (const CfrItem &it : b->plans[(size_t)ri].items_h) cost += it.cost;
+            if (cost > best) best = cost, big = ri;
+        }
+        rc = autotune(b, b->plans[(size_t)big]);
+    }
+    if (rc == PASUR_OK) rc = ensure_aux(ctx);
+    if (rc != PASUR_OK) {
+        free_batch(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PASUR_OK;
+}
+
+int pasur_batch_solve(pasur_batch *b, float *root_util_out, int64_t cap) {
+    if (!b) return PASUR_EINVAL;
+    pasur_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    if (root_util_out && cap < b->n_deals) return set_err(ctx, PASUR_EOVERFLOW, "pasur_batch_solve: cap < n_deals");
+    if (!b->exec) {
+        const int64_t before = ctx->launches;
+        PASUR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = record_sweep(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (rc != PASUR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_err(ctx, e, "pasur_batch_solve: stream capture");
+        b->graph = g;
+        PASUR_CUDA(ctx, cudaGraphInstantiate(&b->exec, g, 0));
+        b->graph_launches = ctx->launches - before;
+    }
+    cudaEvent_t e0, e1;
+    PASUR_CUDA(ctx, cudaEventCreate(&e0));
+    PASUR_CUDA(ctx, cudaEventCreate(&e1));
+    PASUR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+    PASUR_CUDA(ctx, cudaGraphLaunch(b->exec, ctx->stream));
+    ctx->launches += b->graph_launches;
+    PASUR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    int32_t ef = 0;
+    PASUR_CUDA(ctx, cudaMemcpyAsync(&ef, ctx->errflag, sizeof ef, cudaMemcpyDeviceToHost, ctx->stream));
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PASUR_CUDA(ctx, cudaEventElapsedTime(&b->last_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (pasur_tree *t : b->trees) t->iters_done = b->cfg.iters;
+    b->solved = true;
+    if (ef) return set_err(ctx, PASUR_ENUMERIC, "non-finite root value in the batched CFR sweep");
+    if (root_util_out) {
+        bool dev = is_device_ptr(root_util_out);
+        for (int64_t d = 0; d < b->n_deals; d++)
+            PASUR_CUDA(ctx, cudaMemcpyAsync(root_util_out + d, b->util[(size_t)(d * b->n_rounds)], sizeof(float),
+                                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return PASUR_OK;
+}
+
+int pasur_batch_tree(const pasur_batch *b, int64_t deal, int round, pasur_tree **tree_out) {
+    if (!b || !tree_out) return PASUR_EINVAL;
+    if (deal < 0 || deal >= b->n_deals || round < b->first_round || round > 5)
+        return set_err(b->ctx, PASUR_EINVAL, "pasur_batch_tree: deal or round out of range");
+    *tree_out = b->trees[(size_t)(deal * b->n_rounds + (round - b->first_round))];
+    return PASUR_OK;
+}
+
+int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *launches) {
+    if (!b) return PASUR_EINVAL;
+    if (ms) *ms = b->last_ms;
+    if (edges) *edges = b->edges;
+    if (launches) *launches = b->graph_launches;
+    return PASUR_OK;
+}
+
+int pasur_batch_free(pasur_batch *b) {
+    if (!b) return PASUR_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    free_batch(b);
+    delete b;
+    return PASUR_OK;
+}
+
+}  // extern "C"

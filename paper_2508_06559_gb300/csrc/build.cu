@@ -253,7 +253,7 @@ __global__ void k_leaf_values(const GTState *__restrict__ st, const int32_t *__r
         }
     }
     if (!(local_max <= 3.0e38f)) local_max = __int_as_float(0x7f800000);  // non-finite -> +inf
-    atomicMax(umax_bits, __float_as_uint(local_max));
+    if (umax_bits) atomicMax(umax_bits, __float_as_uint(local_max));
 }
 
 unsigned grid_for(int64_t threads, int block) {
@@ -377,6 +377,19 @@ int unfold_levels(pasur_tree *t) {
         if (rc != PASUR_OK) return rc;
         PASUR_TRY(read_i64(ctx, t->fgt_off[k] + m, &t->Q[k]));
     }
+    return PASUR_OK;
+}
+
+// leaf values without any host synchronisation (the batch solver captures this in a CUDA graph);
+// umax_bits (device, may be NULL) receives max |value| as float bits
+int launch_leaf_values(pasur_tree *t, const float *next_util_dev, unsigned *umax_bits) {
+    pasur_ctx *ctx = t->ctx;
+    if (t->M[8] == 0) return PASUR_OK;
+    k_leaf_values<<<grid_for(t->M[8], 256), 256, 0, ctx->stream>>>(t->st[8], t->root[8], t->M[8], t->fgt_off[8],
+                                                                  t->score_off_d, t->scores_d, t->final_round, t->lnk_d,
+                                                                  next_util_dev, t->leaf_v, umax_bits);
+    ctx->launches++;
+    PASUR_CUDA(ctx, cudaGetLastError());
     return PASUR_OK;
 }
 

@@ -36,14 +36,7 @@ constexpr int kClsThreads[kNumCls] = {128, 128, 256, 512, 1024, 256};
 struct CfrParams {
     const CfrItem *items;
     int64_t i_begin, i_end;
-    const CfrRoot *roots;
-    const int32_t *act_li, *act_pl, *act_cs;
-    const uint16_t *act_d;
-    const int64_t *loc_tq;
-    const float *leaf_v;
-    const int64_t *fgt_off0;
-    float *R, *S, *V, *X;
-    double *uacc;
+    const TreeView *views;
     const float *dcfr;  // per iteration: regret factor if R > 0, if R <= 0, strategy-sum factor
     int iters;
     int64_t t0;
@@ -232,8 +225,8 @@ __device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int t0x
 // All T iterations of one item.  RES: the item's arrays are in shared memory (carved from sm);
 // otherwise they are in device memory.
 template <int VARIANT, bool RES>
-__device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, const CfrRoot &cr, const int32_t *s_as,
-                                         float *s_tu, unsigned char *sm) {
+__device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv, const CfrItem &it, const CfrRoot &cr,
+                                         const int32_t *s_as, float *s_tu, unsigned char *sm) {
     const int tid = threadIdx.x, nth = blockDim.x;
     const bool warp0 = tid < 32;
     const int W = it.ns;
@@ -241,8 +234,8 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, 
     const int32_t *Ali, *Apl, *Acs;
     const uint16_t *Ad;
     float *R, *S, *V, *X;
-    const int32_t *gli = p.act_li + cr.act_off, *gpl = p.act_pl + cr.act_off, *gcs = p.act_cs + cr.act_off;
-    const uint16_t *gd = p.act_d + cr.act_off;
+    const int32_t *gli = tv.act_li + cr.act_off, *gpl = tv.act_pl + cr.act_off, *gcs = tv.act_cs + cr.act_off;
+    const uint16_t *gd = tv.act_d + cr.act_off;
     if (RES) {
         size_t o = 0;
         int32_t *sli = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
@@ -259,7 +252,7 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, 
             scs[i] = gcs[i];
             sd[i] = gd[i];
         }
-        const float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
+        const float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
         for (int i = tid; i < L * W; i += nth) {
             R[i] = gR[i];
             S[i] = gS[i];
@@ -273,22 +266,22 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, 
         Apl = gpl;
         Acs = gcs;
         Ad = gd;
-        R = p.R + it.data_base;
-        S = p.S + it.data_base;
-        V = p.V + it.scratch_base;
-        X = p.X + it.scratch_base;
+        R = tv.R + it.data_base;
+        S = tv.S + it.data_base;
+        V = tv.V + it.scratch_base;
+        X = tv.X + it.scratch_base;
     }
     // values of the terminals (leaves and chain heads), constant over the iterations; root reach;
     // per slot the largest |leaf value| of the root's subtree, the scale of the dead zone
     for (int w = tid; w < W; w += nth) s_tu[w] = 0.f;
     __syncthreads();
     {
-        const int64_t *tq = p.loc_tq + cr.loc_off;
+        const int64_t *tq = tv.loc_tq + cr.loc_off;
         for (int x = tid; x < L * W; x += nth) {
             const int li = x / W, w = x - li * W;
             const int64_t q = tq[li];
             if (q >= 0) {
-                const float v = p.leaf_v[q + it.s0 + w];
+                const float v = tv.leaf_v[q + it.s0 + w];
                 V[x] = v;
                 atomicMax((unsigned *)&s_tu[w], __float_as_uint(fabsf(v)));
             }
@@ -340,10 +333,10 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const CfrItem &it, 
     }
     if (tid < W) {
         if (!isfinite(acc)) atomicOr(p.err, 1);
-        p.uacc[p.fgt_off0[it.root] + it.s0 + tid] += acc;
+        tv.uacc[tv.fgt_off0[it.root] + it.s0 + tid] += acc;
     }
     if (RES) {
-        float *gR = p.R + it.data_base, *gS = p.S + it.data_base;
+        float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
         for (int i = tid; i < L * W; i += nth) {
             gR[i] = R[i];
             gS[i] = S[i];
@@ -363,13 +356,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_cfr_items(CfrParams p) {
         if (tid == 0) s_item = atomicAdd(p.counter, 1);
         __syncthreads();
         const int64_t id = p.i_begin + s_item;
-        if (tid < 10) s_as[tid] = id < p.i_end ? p.roots[p.items[id].root].as[tid] : 0;
+        if (tid < 10) s_as[tid] = id < p.i_end ? p.views[p.items[id].tree].roots[p.items[id].root].as[tid] : 0;
         __syncthreads();
         if (id >= p.i_end) break;
         const CfrItem it = p.items[id];
-        const CfrRoot &cr = p.roots[it.root];
-        if (it.scratch_base < 0) run_item<VARIANT, true>(p, it, cr, s_as, s_tu, sm);
-        else run_item<VARIANT, false>(p, it, cr, s_as, s_tu, sm);
+        const TreeView tv = p.views[it.tree];
+        const CfrRoot &cr = tv.roots[it.root];
+        if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, sm);
+        else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, sm);
     }
 }
 
@@ -652,19 +646,15 @@ int build_layout(pasur_tree *t) {
 
 }  // namespace
 
-int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
+int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need) {
     pasur_ctx *ctx = t->ctx;
-    if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
-        return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
     PASUR_TRY(build_layout(t));
-    // plan: every root goes to the smallest shared-memory class its subtree fits with one slot;
-    // its items then take as many slots as that class holds
+    // every root goes to the smallest shared-memory class its subtree fits with one slot; its
+    // items then take as many slots as that class holds
     size_t budget[kNumCls - 1];
     for (int c = 0; c < kNumCls - 1; c++) budget[c] = kClsBudget[c] ? std::min<size_t>(kClsBudget[c], ctx->smem_optin) : ctx->smem_optin;
     const int wcap = cfg->slots_per_item > 0 ? std::min(cfg->slots_per_item, kMaxSlots) : kMaxSlots;
-    std::vector<CfrItem> cls_items[kNumCls];
     int64_t data = 0, scratch = 0;
-    size_t need[kNumCls] = {0};
     for (int64_t g = 0; g < t->n_roots; g++) {
         CfrRoot &cr = t->croots_h[(size_t)g];
         const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
@@ -686,6 +676,7 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
         for (int64_t s0 = 0; s0 < Sg; s0 += w) {
             CfrItem it{};
             it.root = (int32_t)g;
+            it.tree = tree;
             it.ns = (int32_t)std::min<int64_t>(w, Sg - s0);
             it.s0 = s0;
             it.data_base = data;
@@ -701,26 +692,11 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
             cls_items[cls].push_back(it);
         }
     }
-    t->items_h.clear();
-    for (int c = 0; c < kNumCls; c++) {
-        std::stable_sort(cls_items[c].begin(), cls_items[c].end(),
-                         [](const CfrItem &a, const CfrItem &b) { return a.cost > b.cost; });
-        t->cls_begin[c] = (int64_t)t->items_h.size();
-        t->items_h.insert(t->items_h.end(), cls_items[c].begin(), cls_items[c].end());
-        t->cls_end[c] = (int64_t)t->items_h.size();
-        t->cls_smem[c] = need[c];
-    }
-    t->n_items = (int64_t)t->items_h.size();
     t->data_size = data;
     t->scratch_size = scratch;
     if (t->n_roots > 0)
         PASUR_CUDA(ctx, cudaMemcpyAsync(t->croots_d, t->croots_h.data(), sizeof(CfrRoot) * (size_t)t->n_roots,
                                         cudaMemcpyHostToDevice, ctx->stream));
-    if (t->n_items) {
-        PASUR_TRY(tree_alloc(t, (void **)&t->items_d, sizeof(CfrItem) * (size_t)t->n_items));
-        PASUR_CUDA(ctx, cudaMemcpyAsync(t->items_d, t->items_h.data(), sizeof(CfrItem) * (size_t)t->n_items,
-                                        cudaMemcpyHostToDevice, ctx->stream));
-    }
     PASUR_TRY(tree_alloc(t, (void **)&t->R, sizeof(float) * (size_t)(data + 1)));
     PASUR_TRY(tree_alloc(t, (void **)&t->S, sizeof(float) * (size_t)(data + 1)));
     PASUR_CUDA(ctx, cudaMemsetAsync(t->R, 0, sizeof(float) * (size_t)(data + 1), ctx->stream));
@@ -731,9 +707,53 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
     }
     PASUR_TRY(tree_alloc(t, (void **)&t->uacc, sizeof(double) * (size_t)(t->Q[0] + 1)));
     PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
-    // persistent grid per class
+    TreeView &v = t->view;
+    v.roots = t->croots_d;
+    v.act_li = t->act_li;
+    v.act_pl = t->act_pl;
+    v.act_cs = t->act_cs;
+    v.act_d = t->act_d;
+    v.loc_tq = t->loc_tq;
+    v.leaf_v = t->leaf_v;
+    v.fgt_off0 = t->fgt_off[0];
+    v.R = t->R;
+    v.S = t->S;
+    v.V = t->V;
+    v.X = t->X;
+    v.uacc = t->uacc;
+    t->iters_done = 0;
+    t->cfr_ready = true;
+    return PASUR_OK;
+}
+
+int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
+                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned) {
+    if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
+        return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
+    plan.items_h.clear();
+    for (int c = 0; c < kNumCls; c++) {
+        std::stable_sort(cls_items[c].begin(), cls_items[c].end(),
+                         [](const CfrItem &a, const CfrItem &b) { return a.cost > b.cost; });
+        plan.cls_begin[c] = (int64_t)plan.items_h.size();
+        plan.items_h.insert(plan.items_h.end(), cls_items[c].begin(), cls_items[c].end());
+        plan.cls_end[c] = (int64_t)plan.items_h.size();
+        plan.cls_smem[c] = need[c];
+    }
+    plan.n_items = (int64_t)plan.items_h.size();
+    if (plan.n_items) {
+        size_t b = sizeof(CfrItem) * (size_t)plan.n_items;
+        PASUR_TRY(dev_alloc(ctx, (void **)&plan.items_d, b));
+        owned.push_back({plan.items_d, b});
+        PASUR_CUDA(ctx, cudaMemcpyAsync(plan.items_d, plan.items_h.data(), b, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (!views.empty()) {
+        size_t b = sizeof(TreeView) * views.size();
+        PASUR_TRY(dev_alloc(ctx, (void **)&plan.views_d, b));
+        owned.push_back({plan.views_d, b});
+        PASUR_CUDA(ctx, cudaMemcpyAsync(plan.views_d, views.data(), b, cudaMemcpyHostToDevice, ctx->stream));
+    }
     size_t max_sm = 0;
-    for (int c = 0; c < kNumCls; c++) max_sm = std::max(max_sm, t->cls_smem[c]);
+    for (int c = 0; c < kNumCls; c++) max_sm = std::max(max_sm, plan.cls_smem[c]);
     if (max_sm > 48 * 1024) {
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
@@ -741,144 +761,177 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
     }
     for (int c = 0; c < kNumCls; c++) {
-        t->cls_blocks[c] = 0;
+        plan.cls_blocks[c] = 0;
         const int threads = cfg->threads > 0 ? cfg->threads : kClsThreads[c];
-        t->cls_threads[c] = threads;
-        int64_t n = t->cls_end[c] - t->cls_begin[c];
+        plan.cls_threads[c] = threads;
+        int64_t n = plan.cls_end[c] - plan.cls_begin[c];
         if (n == 0) continue;
         int per_sm = 0;
         if (threads <= 256)
-            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, t->cls_smem[c]));
+            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, plan.cls_smem[c]));
         else
-            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, t->cls_smem[c]));
+            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, plan.cls_smem[c]));
         if (per_sm < 1) return set_err(ctx, PASUR_EINVAL, "CFR kernel cannot be resident with this shared-memory plan");
-        t->cls_blocks[c] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n));
+        plan.cls_blocks[c] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n));
     }
-    if (getenv("PASUR_VERBOSE")) {
-        int64_t ne = 0;
-        for (int k = 1; k < 9; k++) ne += t->Q[k];
-        fprintf(stderr, "[pasur] round %d: GT roots %lld, FGT edges %lld, local %lld, active %lld, items %lld\n", t->round,
-                (long long)t->n_roots, (long long)ne, (long long)t->n_local, (long long)t->n_active, (long long)t->n_items);
-        for (int c = 0; c < kNumCls; c++) {
-            int64_t n = t->cls_end[c] - t->cls_begin[c];
-            if (!n) continue;
-            int64_t cost = 0;
-            for (int64_t i = t->cls_begin[c]; i < t->cls_end[c]; i++) cost += t->items_h[(size_t)i].cost;
-            fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld\n",
-                    c, (long long)n, t->cls_smem[c], t->cls_blocks[c], t->cls_threads[c], (long long)cost);
-        }
+    return PASUR_OK;
+}
+
+int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks) {
+    int per_sm = 0;
+    if (threads <= 256)
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, smem));
+    else
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, smem));
+    *blocks = per_sm < 1 ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n_items));
+    return PASUR_OK;
+}
+
+int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float **out, size_t *bytes) {
+    *out = nullptr;
+    *bytes = 0;
+    if (cfg->variant != 1 || cfg->iters <= 0) return PASUR_OK;
+    std::vector<float> f(3 * (size_t)cfg->iters);
+    for (int i = 0; i < cfg->iters; i++) {
+        double tt = (double)(t0 + i + 1), tp = tt - 1.0;
+        double pa = std::pow(tp, (double)cfg->dcfr_alpha), pb = std::pow(tp, (double)cfg->dcfr_beta);
+        f[3 * i] = (float)(pa / (pa + 1.0));
+        f[3 * i + 1] = (float)(pb / (pb + 1.0));
+        f[3 * i + 2] = (float)(tt > 1.0 ? std::pow(1.0 - 1.0 / tt, (double)cfg->dcfr_gamma) : 0.0);
     }
-    t->iters_done = 0;
-    t->cfr_ready = true;
+    *bytes = f.size() * sizeof(float);
+    PASUR_TRY(dev_alloc(ctx, (void **)out, *bytes));
+    PASUR_CUDA(ctx, cudaMemcpyAsync(*out, f.data(), *bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return PASUR_OK;
+}
+
+int ensure_aux(pasur_ctx *ctx) {
+    if (ctx->fork) return PASUR_OK;
+    PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    for (int c = 0; c < kNumCls; c++) {
+        PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
+        PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
+        PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
+        PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t1[c]));
+    }
+    return PASUR_OK;
+}
+
+int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int64_t t0, const float *dcfr) {
+    if (cfg->iters <= 0 || plan.n_items == 0) return PASUR_OK;
+    PASUR_TRY(ensure_aux(ctx));
+    CfrParams p{};
+    p.items = plan.items_d;
+    p.views = plan.views_d;
+    p.dcfr = dcfr;
+    p.iters = cfg->iters;
+    p.t0 = t0;
+    p.tau = cfg->rm_deadzone;
+    p.err = ctx->errflag;
+    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int32_t) * kNumCls, ctx->stream));
+    PASUR_CUDA(ctx, cudaEventRecord(ctx->fork, ctx->stream));
+    // the classes are independent: each runs on its own forked stream, largest subtrees first
+    for (int oi = 0; oi < kNumCls; oi++) {
+        const int c = kNumCls - 1 - oi;
+        if (plan.cls_end[c] == plan.cls_begin[c]) continue;
+        cudaStream_t st = ctx->aux[c];
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
+        p.i_begin = plan.cls_begin[c];
+        p.i_end = plan.cls_end[c];
+        p.counter = ctx->counter + c;
+        const bool wide = plan.cls_threads[c] > 256;
+        if (cfg->variant == 1 && wide)
+            k_cfr_items<1, 1024><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
+        else if (cfg->variant == 1)
+            k_cfr_items<1, 256><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
+        else if (wide)
+            k_cfr_items<0, 1024><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
+        else
+            k_cfr_items<0, 256><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
+    }
+    return PASUR_OK;
+}
+
+void cfr_plan_times(pasur_ctx *ctx, CfrPlan &plan) {
+    for (int c = 0; c < kNumCls; c++) {
+        float m = 0.f;
+        if (plan.cls_end[c] != plan.cls_begin[c]) cudaEventElapsedTime(&m, ctx->cls_t0[c], ctx->cls_t1[c]);
+        plan.cls_ms[c] = m;
+    }
+}
+
+static void print_plan(const pasur_tree *t, const CfrPlan &plan) {
+    int64_t ne = 0;
+    for (int k = 1; k < 9; k++) ne += t->Q[k];
+    fprintf(stderr, "[pasur] round %d: GT roots %lld, FGT edges %lld, local %lld, active %lld, items %lld\n", t->round,
+            (long long)t->n_roots, (long long)ne, (long long)t->n_local, (long long)t->n_active, (long long)plan.n_items);
+    for (int c = 0; c < kNumCls; c++) {
+        int64_t n = plan.cls_end[c] - plan.cls_begin[c];
+        if (!n) continue;
+        int64_t cost = 0;
+        for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) cost += plan.items_h[(size_t)i].cost;
+        fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld\n", c,
+                (long long)n, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost);
+    }
+}
+
+int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
+    pasur_ctx *ctx = t->ctx;
+    std::vector<CfrItem> cls_items[kNumCls];
+    size_t need[kNumCls] = {0};
+    PASUR_TRY(cfr_setup_tree(t, cfg, 0, cls_items, need));
+    std::vector<std::pair<void *, size_t>> owned;
+    int rc = cfr_finalize_plan(ctx, t->plan, cls_items, need, {t->view}, cfg, owned);
+    for (auto &o : owned) {
+        t->allocs.push_back(o.first);
+        t->allocs.push_back((void *)(uintptr_t)o.second);
+    }
+    if (rc != PASUR_OK) return rc;
+    if (getenv("PASUR_VERBOSE")) print_plan(t, t->plan);
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return PASUR_OK;
 }
 
 int cfr_run(pasur_tree *t, const pasur_config *cfg) {
     pasur_ctx *ctx = t->ctx;
-    if (cfg->iters <= 0 || t->n_items == 0) {
+    if (cfg->iters <= 0 || t->plan.n_items == 0) {
         t->last_ms = 0.f;
         t->last_launches = 0;
         return PASUR_OK;
     }
     float *dcfr = nullptr;
     size_t db = 0;
-    if (cfg->variant == 1) {
-        std::vector<float> f(3 * (size_t)cfg->iters);
-        for (int i = 0; i < cfg->iters; i++) {
-            double tt = (double)(t->iters_done + i + 1), tp = tt - 1.0;
-            double pa = std::pow(tp, (double)cfg->dcfr_alpha), pb = std::pow(tp, (double)cfg->dcfr_beta);
-            f[3 * i] = (float)(pa / (pa + 1.0));
-            f[3 * i + 1] = (float)(pb / (pb + 1.0));
-            f[3 * i + 2] = (float)(tt > 1.0 ? std::pow(1.0 - 1.0 / tt, (double)cfg->dcfr_gamma) : 0.0);
-        }
-        db = f.size() * sizeof(float);
-        PASUR_TRY(dev_alloc(ctx, (void **)&dcfr, db));
-        PASUR_CUDA(ctx, cudaMemcpyAsync(dcfr, f.data(), db, cudaMemcpyHostToDevice, ctx->stream));
-    }
-    CfrParams p{};
-    p.items = t->items_d;
-    p.roots = t->croots_d;
-    p.act_li = t->act_li;
-    p.act_pl = t->act_pl;
-    p.act_cs = t->act_cs;
-    p.act_d = t->act_d;
-    p.loc_tq = t->loc_tq;
-    p.leaf_v = t->leaf_v;
-    p.fgt_off0 = t->fgt_off[0];
-    p.R = t->R;
-    p.S = t->S;
-    p.V = t->V;
-    p.X = t->X;
-    p.uacc = t->uacc;
-    p.dcfr = dcfr;
-    p.iters = cfg->iters;
-    p.t0 = t->iters_done;
-    p.tau = cfg->rm_deadzone;
-    p.err = ctx->errflag;
-    if (!ctx->fork) {
-        PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
-        for (int c = 0; c < kNumCls; c++) {
-            PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
-            PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
-            PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
-            PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t1[c]));
-        }
-    }
+    PASUR_TRY(cfr_dcfr_factors(ctx, cfg, t->iters_done, &dcfr, &db));
     cudaEvent_t e0, e1;
     PASUR_CUDA(ctx, cudaEventCreate(&e0));
     PASUR_CUDA(ctx, cudaEventCreate(&e1));
-    PASUR_CUDA(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int32_t) * kNumCls, ctx->stream));
     PASUR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int32_t), ctx->stream));
     PASUR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-    PASUR_CUDA(ctx, cudaEventRecord(ctx->fork, ctx->stream));
-    int launches = 0;
-    // the classes are independent: each runs on its own forked stream, largest subtrees first
-    for (int oi = 0; oi < kNumCls; oi++) {
-        const int c = kNumCls - 1 - oi;
-        if (t->cls_end[c] == t->cls_begin[c]) continue;
-        cudaStream_t st = ctx->aux[c];
-        PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
-        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
-        p.i_begin = t->cls_begin[c];
-        p.i_end = t->cls_end[c];
-        p.counter = ctx->counter + c;
-        const bool wide = t->cls_threads[c] > 256;
-        if (cfg->variant == 1 && wide)
-            k_cfr_items<1, 1024><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
-        else if (cfg->variant == 1)
-            k_cfr_items<1, 256><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
-        else if (wide)
-            k_cfr_items<0, 1024><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
-        else
-            k_cfr_items<0, 256><<<t->cls_blocks[c], t->cls_threads[c], t->cls_smem[c], st>>>(p);
-        ctx->launches++;
-        launches++;
-        PASUR_CUDA(ctx, cudaGetLastError());
-        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
-        PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
-        PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
-    }
+    const int64_t before = ctx->launches;
+    int rc = cfr_launch_plan(ctx, t->plan, cfg, t->iters_done, dcfr);
+    if (rc != PASUR_OK) return rc;
     PASUR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
     int32_t ef = 0;
     PASUR_CUDA(ctx, cudaMemcpyAsync(&ef, ctx->errflag, sizeof ef, cudaMemcpyDeviceToHost, ctx->stream));
     PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     PASUR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
-    for (int c = 0; c < kNumCls; c++) {
-        float m = 0.f;
-        if (t->cls_end[c] != t->cls_begin[c]) cudaEventElapsedTime(&m, ctx->cls_t0[c], ctx->cls_t1[c]);
-        t->cls_ms[c] = m;
-    }
+    cfr_plan_times(ctx, t->plan);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (dcfr) dev_free(ctx, dcfr, db);
     t->last_ms = ms;
-    t->last_launches = launches;
+    t->last_launches = (int32_t)(ctx->launches - before);
     t->iters_done += cfg->iters;
     if (getenv("PASUR_VERBOSE")) {
         fprintf(stderr, "[pasur] round %d: %d iterations in %.3f ms (", t->round, cfg->iters, ms);
-        for (int c = 0; c < kNumCls; c++) fprintf(stderr, "%s%.2f", c ? " " : "", t->cls_ms[c]);
+        for (int c = 0; c < kNumCls; c++) fprintf(stderr, "%s%.2f", c ? " " : "", t->plan.cls_ms[c]);
         fprintf(stderr, " ms per class)\n");
     }
     if (ef) return set_err(ctx, PASUR_ENUMERIC, "non-finite root value in the CFR sweep");
@@ -901,20 +954,22 @@ int cfr_export_sigma(const pasur_tree *t, float *out_dev) {
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }
-    if (t->n_items) {
-        unsigned g = (unsigned)std::min<int64_t>(t->n_items, 65535);
-        k_export_sigma<<<g, 256, 0, ctx->stream>>>(t->items_d, t->n_items, t->croots_d, t->act_cs, t->act_d, t->act_gt, t->S,
-                                                   lp, out_dev);
+    if (t->plan.n_items) {
+        unsigned g = (unsigned)std::min<int64_t>(t->plan.n_items, 65535);
+        k_export_sigma<<<g, 256, 0, ctx->stream>>>(t->plan.items_d, t->plan.n_items, t->croots_d, t->act_cs, t->act_d,
+                                                   t->act_gt, t->S, lp, out_dev);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }
     return PASUR_OK;
 }
 
-int cfr_export_utilities(const pasur_tree *t, float *out_dev) {
+int cfr_export_utilities(const pasur_tree *t, float *out_dev) { return cfr_export_utilities_n(t, t->iters_done, out_dev); }
+
+int cfr_export_utilities_n(const pasur_tree *t, int64_t iters, float *out_dev) {
     pasur_ctx *ctx = t->ctx;
     if (t->Q[0] == 0) return PASUR_OK;
-    double inv = t->iters_done > 0 ? 1.0 / (double)t->iters_done : 0.0;
+    double inv = iters > 0 ? 1.0 / (double)iters : 0.0;
     k_export_util<<<grid_for(t->Q[0], 256), 256, 0, ctx->stream>>>(t->uacc, t->Q[0], inv, out_dev);
     ctx->launches++;
     PASUR_CUDA(ctx, cudaGetLastError());

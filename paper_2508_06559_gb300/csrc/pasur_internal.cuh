@@ -139,13 +139,40 @@ struct CfrRoot {
     int64_t item0;            // index of its first work item
 };
 
+// Per-tree pointers of the CFR kernel (one entry per round tree of a launch).
+struct TreeView {
+    const CfrRoot *roots;
+    const int32_t *act_li, *act_pl, *act_cs;
+    const uint16_t *act_d;
+    const int64_t *loc_tq;
+    const float *leaf_v;
+    const int64_t *fgt_off0;
+    float *R, *S, *V, *X;
+    double *uacc;
+};
+
 struct CfrItem {              // one work item of the CFR kernel: a root and a run of its slots
     int32_t root;
+    int32_t tree;             // index into the launch's TreeView table
     int32_t ns;               // slots in the item
+    int32_t pad;
     int64_t s0;               // first slot of the item within its root
     int64_t data_base;        // offset of the item's (local node, slot) table in R and S
     int64_t scratch_base;     // offset in the global transients, or -1 when the item is resident
     int64_t cost;             // active nodes * slots, for the schedule
+};
+
+// A CFR launch plan: work items of one or more trees merged per shared-memory class.
+struct CfrPlan {
+    std::vector<CfrItem> items_h;       // ordered by class, then cost (largest first)
+    CfrItem *items_d = nullptr;
+    TreeView *views_d = nullptr;
+    int64_t n_items = 0;
+    int64_t cls_begin[8] = {0}, cls_end[8] = {0};
+    size_t cls_smem[8] = {0};
+    int cls_blocks[8] = {0};
+    int cls_threads[8] = {0};
+    float cls_ms[8] = {0};
 };
 
 struct pasur_tree {
@@ -193,14 +220,9 @@ struct pasur_tree {
     int64_t *act_gt = nullptr;          //   GT node index
     int64_t *loc_tq = nullptr;          // per local node: FGT index (slot 0) of its chain's leaf, -1 if active
     int64_t n_local = 0, n_active = 0;
-    std::vector<CfrItem> items_h;       // ordered by launch class, then cost
-    CfrItem *items_d = nullptr;
-    int64_t n_items = 0, data_size = 0, scratch_size = 0;
-    int64_t cls_begin[8] = {0}, cls_end[8] = {0};
-    size_t cls_smem[8] = {0};
-    int cls_blocks[8] = {0};
-    int cls_threads[8] = {0};
-    float cls_ms[8] = {0};
+    CfrPlan plan;                       // this tree alone
+    TreeView view{};                    // its pointers for the CFR kernel
+    int64_t data_size = 0, scratch_size = 0;
     float *R = nullptr, *S = nullptr;   // per (local node, slot) of every item
     float *V = nullptr, *X = nullptr;   // values and reaches of the non-resident items
     double *uacc = nullptr;             // Q[0]
@@ -249,12 +271,28 @@ int ensure_capture_table(pasur_ctx *ctx);
 int build_levels(pasur_tree *t, const uint64_t *root_pools_dev);
 int unfold_levels(pasur_tree *t);
 int compute_leaf_values(pasur_tree *t, const float *next_util_dev);
+int launch_leaf_values(pasur_tree *t, const float *next_util_dev, unsigned *umax_bits);
 
 // cfr.cu
 int cfr_prepare(pasur_tree *t, const pasur_config *cfg);
 int cfr_run(pasur_tree *t, const pasur_config *cfg);
+// layout, per-root plan and state of one tree; its items (tagged with tree index `tree`) are
+// appended per class to cls_items, the shared-memory need per class raised in need[]
+int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need);
+// sort and upload merged items and the tree views; launch configuration per class
+int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
+                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned);
+// launch the plan's classes for cfg->iters iterations starting at iteration t0 (+1); no host
+// synchronisation (capturable); per-class times are read by cfr_plan_times
+int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int64_t t0, const float *dcfr);
+void cfr_plan_times(pasur_ctx *ctx, CfrPlan &plan);
+int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float **out, size_t *bytes);
+// blocks of a persistent CFR launch with this block size and shared memory (0 if it cannot run)
+int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks);
 int cfr_export_sigma(const pasur_tree *t, float *out_dev);
 int cfr_export_utilities(const pasur_tree *t, float *out_dev);
+int cfr_export_utilities_n(const pasur_tree *t, int64_t iters, float *out_dev);
+int ensure_aux(pasur_ctx *ctx);
 
 // between.cu
 int next_roots(pasur_tree *t, std::vector<uint64_t> &pools, std::vector<int64_t> &score_off,

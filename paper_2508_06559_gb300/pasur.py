@@ -27,7 +27,8 @@ EXPORTS = [
     "pasur_deal",
     "pasur_build_round", "pasur_tree_free", "pasur_tree_sizes", "pasur_unfold", "pasur_cfr_iterate",
     "pasur_avg_strategy", "pasur_round_utilities", "pasur_next_roots", "pasur_export_level", "pasur_leaf_values",
-    "pasur_last_cfr_stats", "pasur_move_offsets_noalloc",
+    "pasur_last_cfr_stats", "pasur_batch_create", "pasur_batch_solve", "pasur_batch_tree", "pasur_batch_stats",
+    "pasur_batch_free", "pasur_move_offsets_noalloc",
 ]
 
 
@@ -81,6 +82,11 @@ def load() -> C.CDLL:
     L.pasur_leaf_values.argtypes = [vp, vp, i64]
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
+    L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
+    L.pasur_batch_solve.argtypes = [vp, vp, i64]
+    L.pasur_batch_tree.argtypes = [vp, i64, C.c_int, C.POINTER(vp)]
+    L.pasur_batch_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, i64p]
+    L.pasur_batch_free.argtypes = [vp]
     for name in EXPORTS:
         if name != "pasur_last_error":
             getattr(L, name).restype = C.c_int
@@ -142,12 +148,15 @@ class Ctx:
         _check(rc, None)
         self.h = h
         self._trees = weakref.WeakSet()
+        self._batches = weakref.WeakSet()
 
     def close(self):
-        """Free the context's remaining trees, then the context."""
+        """Free the context's remaining trees and batches, then the context."""
         if self.h:
             for t in list(self._trees):
                 t.free()
+            for b in list(self._batches):
+                b.free()
             _check(load().pasur_destroy(self.h), self.h)
             self.h = None
 
@@ -178,14 +187,53 @@ class Ctx:
         return t
 
 
-class Tree:
-    """One round: wraps the pasur_tree calls (names as in the C ABI)."""
+class Batch:
+    """pasur_batch_create / _solve / _tree / _stats / _free: many deals solved together."""
 
-    def __init__(self, ctx: Ctx, h):
-        self.ctx, self.h = ctx, h
+    def __init__(self, ctx: Ctx, decks, first_round: int, cfg: pasur_config):
+        d = np.ascontiguousarray(np.asarray(decks, np.uint8).reshape(-1, 52))
+        h = vp()
+        _check(load().pasur_batch_create(ctx.h, _ptr(d), d.shape[0], first_round, C.byref(cfg), C.byref(h)), ctx.h)
+        self.ctx, self.h, self.n_deals, self.first_round = ctx, h, d.shape[0], first_round
+        ctx._batches.add(self)
 
     def free(self):
         if self.h and self.ctx.h:
+            load().pasur_batch_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def pasur_batch_solve(self, out=None):
+        if out is None:
+            out = np.zeros(self.n_deals, np.float32)
+        n = out.numel() if hasattr(out, "numel") else len(out)
+        _check(load().pasur_batch_solve(self.h, _ptr(out), n), self.ctx.h)
+        return out
+
+    def pasur_batch_tree(self, deal: int, rnd: int) -> "Tree":
+        th = vp()
+        _check(load().pasur_batch_tree(self.h, deal, rnd, C.byref(th)), self.ctx.h)
+        return Tree(self.ctx, th, owned=False)
+
+    def pasur_batch_stats(self):
+        ms, e, l = C.c_float(0), C.c_int64(0), C.c_int64(0)
+        _check(load().pasur_batch_stats(self.h, C.byref(ms), C.byref(e), C.byref(l)), self.ctx.h)
+        return ms.value, e.value, l.value
+
+
+class Tree:
+    """One round: wraps the pasur_tree calls (names as in the C ABI)."""
+
+    def __init__(self, ctx: Ctx, h, owned: bool = True):
+        self.ctx, self.h, self.owned = ctx, h, owned
+
+    def free(self):
+        if self.h and self.ctx.h and self.owned:
             load().pasur_tree_free(self.h)
         self.h = None
 

@@ -1,0 +1,100 @@
+"""Batched solve of several deals (one merged persistent launch per round and size class, under a
+captured CUDA graph) against the per-tree path and the oracle.
+
+Every work item's arithmetic depends only on its own subtree, so the batch must reproduce the
+per-tree solves bit for bit whatever block sizes the autotuner picks and whichever deals share a
+launch; replaying the graph must reproduce the first solve bit for bit; and the deals' root values
+must match the oracle's chained solve of the same rounds.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SEEDS = [0, 1, 2, 5, 9]
+FIRST, T = 4, 300
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2508_06559_gb300 import build as B
+    from paper_2508_06559_gb300 import pasur as P
+    B.build()
+    c = P.Ctx(0)
+    yield c
+    c.close()
+
+
+def P():
+    from paper_2508_06559_gb300 import pasur
+    return pasur
+
+
+def mask_ids(ids):
+    m = 0
+    for c in ids:
+        m |= 1 << int(c)
+    return m
+
+
+def per_tree_solve(ctx, deck, first, cfg):
+    """The same rounds through the single-tree entry points."""
+    pools, soff, scores = [mask_ids(deck[:4])], [0, 1], [[0, 0, 0, 0]]
+    trees = []
+    for r in range(first, 6):
+        t = ctx.pasur_build_round(deck, r, pools)
+        t.pasur_unfold(soff, scores)
+        trees.append(t)
+        if r < 5:
+            pools, soff, scores, _ = t.pasur_next_roots()
+    nxt, out = None, {}
+    for i in range(len(trees) - 1, -1, -1):
+        trees[i].pasur_cfr_iterate(cfg, nxt)
+        out[first + i] = (trees[i].pasur_round_utilities(), trees[i].pasur_avg_strategy())
+        nxt = out[first + i][0]
+    for t in trees:
+        t.free()
+    return out
+
+
+def test_batch_equals_per_tree_and_replays(ctx):
+    decks = np.stack([O.deal(s) for s in SEEDS])
+    cfg = P().pasur_config_default(iters=T)
+    b = P().Batch(ctx, decks, FIRST, cfg)
+    u1 = b.pasur_batch_solve()
+    got = {(d, r): (b.pasur_batch_tree(d, r).pasur_round_utilities(), b.pasur_batch_tree(d, r).pasur_avg_strategy())
+           for d in range(len(SEEDS)) for r in range(FIRST, 6)}
+    u2 = b.pasur_batch_solve()  # graph replay
+    assert (u1 == u2).all()
+    ms, edges, launches = b.pasur_batch_stats()
+    assert ms > 0 and edges > 0 and launches > 0
+    for d, s in enumerate(SEEDS):
+        ref = per_tree_solve(ctx, decks[d], FIRST, cfg)
+        for r in range(FIRST, 6):
+            assert (got[(d, r)][0] == ref[r][0]).all(), (s, r)
+            assert (got[(d, r)][1] == ref[r][1]).all(), (s, r)
+        assert u1[d] == ref[FIRST][0][0]
+    b.free()
+
+
+def test_batch_root_values_match_oracle_chain(ctx):
+    """Each side chains its own round-5 utilities into round 4 (f32 vs fp64 end to end)."""
+    decks = np.stack([O.deal(s) for s in SEEDS[:3]])
+    cfg = P().pasur_config_default(iters=T)
+    b = P().Batch(ctx, decks, FIRST, cfg)
+    u = b.pasur_batch_solve()
+    b.free()
+    for d in range(len(decks)):
+        deck = decks[d]
+        o4 = O.Tree(deck, 4, [mask_ids(deck[:4])])
+        o4.unfold_single()
+        op, os_, osc, ol = o4.next_roots()
+        o5 = O.Tree(deck, 5, op)
+        o5.unfold(os_, osc)
+        _, U5 = o5.cfr(o5.leaf_utilities_final(), T)
+        _, U4 = o4.cfr(o4.leaf_utilities_linked(ol, U5), T)
+        assert abs(float(u[d]) - U4[0]) < 1e-4, (d, float(u[d]), U4[0])
