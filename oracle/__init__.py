@@ -87,6 +87,13 @@ def lib():
         L.or_count_round.argtypes = [u8p, C.c_int, C.c_uint64, i64p]
         L.or_minimax_rounds.argtypes = [u8p, C.c_int, C.c_uint64, i16p]
         L.or_minimax_rounds.restype = C.c_double
+        L.or_philox4x64.argtypes = [u64p, u64p, u64p]
+        L.or_selfplay.argtypes = [P(C.c_void_p), C.c_int, P(P(C.c_float)), P(i64p), C.c_int64, C.c_int64,
+                                  C.c_uint64, i16p]
+        L.or_selfplay.restype = C.c_int
+        L.or_outcome_distribution.argtypes = [P(C.c_void_p), C.c_int, P(f64p), P(i64p), C.c_int64, C.c_int,
+                                              C.c_int, f64p]
+        L.or_outcome_distribution.restype = C.c_int
         _lib = L
     return _lib
 
@@ -327,3 +334,48 @@ class Tree:
 
 
 MINIMAX, BR_ALEX, BR_BOB, ON_POLICY, UNIFORM = 0, 1, 2, 3, 4
+
+
+# ---------------------------------------------------------------------------------------------
+# Self-play (fair-value simulation; one sampled move per parent, §External Sampling)
+# ---------------------------------------------------------------------------------------------
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    """Philox4x64-10 of one counter block (Salmon et al., SC 2011)."""
+    c = np.ascontiguousarray(ctr, np.uint64)
+    k = np.ascontiguousarray(key, np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().or_philox4x64(_p(c, u64p), _p(k, u64p), _p(out, u64p))
+    return out
+
+
+def _chain(trees, per_round, ctype, np_type):
+    arrs = [np.ascontiguousarray(a, np_type) for a in per_round]
+    ptrs = (P(ctype) * len(arrs))(*[a.ctypes.data_as(P(ctype)) for a in arrs])
+    return arrs, ptrs
+
+
+def selfplay(trees, sigmas, lnks, root_q: int, n_games: int, seed: int) -> np.ndarray:
+    """Final game differences of n_games sampled games from FGT root root_q of trees[0] through
+    the rounds of `trees` (the last one final).  sigmas: per round, float32 strategy of every FGT
+    edge (levels 1..8); lnks: per non-final round, its leaf-to-next-root links."""
+    hs = (C.c_void_p * len(trees))(*[t._h for t in trees])
+    sg, sp = _chain(trees, sigmas, C.c_float, np.float32)
+    lk, lp = _chain(trees, list(lnks) + [np.zeros(1, np.int64)], C.c_int64, np.int64)
+    out = np.zeros(n_games, np.int16)
+    if lib().or_selfplay(hs, len(trees), sp, lp, root_q, n_games, seed, _p(out, i16p)) != 0:
+        raise ValueError("or_selfplay: invalid arguments")
+    return out
+
+
+def outcome_distribution(trees, sigmas, lnks, root_q: int, lo: int = -128, n_bins: int = 257) -> np.ndarray:
+    """Exact probabilities of the final game differences lo .. lo+n_bins-1 when both players
+    follow sigmas (float64, laid out as for selfplay)."""
+    hs = (C.c_void_p * len(trees))(*[t._h for t in trees])
+    sg, sp = _chain(trees, sigmas, C.c_double, np.float64)
+    lk, lp = _chain(trees, list(lnks) + [np.zeros(1, np.int64)], C.c_int64, np.int64)
+    prob = np.zeros(n_bins, np.float64)
+    if lib().or_outcome_distribution(hs, len(trees), sp, lp, root_q, lo, n_bins, _p(prob, f64p)) != 0:
+        raise ValueError("or_outcome_distribution: invalid arguments or difference out of range")
+    return prob

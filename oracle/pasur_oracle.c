@@ -18,6 +18,11 @@
  *   or_cfr                                 pinned (T=1 closed form; minimax convergence; LP value;
  *                                          regret identity; zero-sum / delta invariance)
  *   or_minimax / or_best_response          pinned (scipy LP on tiny subgames; BR_B <= v <= BR_A)
+ *   or_philox4x64                          pinned (numpy's Philox bit generator, a library routine)
+ *   or_selfplay                            pinned (sample mean and outcome frequencies against the
+ *                                          exact values below; pure strategies give one game)
+ *   or_outcome_distribution                pinned (its mean equals the on-policy root value of
+ *                                          or_root_values chained over the rounds; sums to 1)
  *
  * Conventions (the paper's, restated):
  *   card id = 4*rank + suit, rank 0 = Ace .. 9 = Ten, 10 = J, 11 = Q, 12 = K; suit 0 = clubs,
@@ -952,4 +957,165 @@ double or_minimax_rounds(const uint8_t *deck, int round, uint64_t pool, const in
     uint64_t st[3] = {hand_mask(deck, 4 + 8 * round), hand_mask(deck, 8 + 8 * round), pool};
     int8_t rus[7] = {0};
     return mm_rec(deck, round, st, rus, score, 0);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Self-play (the fair-value simulation of the paper's introduction and its learned-strategy   */
+/* study): games played from one FGT root through consecutive rounds, every move drawn from    */
+/* the average strategy of the node reached, one choice per parent as in §External Sampling.   */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Philox4x64-10, written from its published definition (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC 2011): ten rounds of two 64x64->128-bit
+ * multiplications by fixed odd constants, the high halves xored with the other two counter
+ * words and the round key, the key bumped by the two Weyl constants between rounds.
+ */
+void or_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The uniform draw of ply `ply` of game `game`: word 0 of Philox4x64-10 at counter
+ * (ply, game, 0, 0) under key (seed, 0), its top 24 bits as a float in [0, 1). */
+static float sp_uniform(uint64_t seed, int64_t game, int64_t ply) {
+    uint64_t ctr[4] = {(uint64_t)ply, (uint64_t)game, 0, 0}, key[2] = {seed, 0}, o[4];
+    or_philox4x64(ctr, key, o);
+    return (float)(o[0] >> 40) * (1.0f / 16777216.0f);
+}
+
+/* Index of the GT root that owns FGT root q (fgt_off[0] is ascending). */
+static int64_t gt_root_of(const or_tree *t, int64_t q) {
+    int64_t lo = 0, hi = t->n[0] - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (t->fgt_off[0][mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* The final game difference at FGT leaf (j, s) of the final round: the score difference after
+ * the round (inherited difference + the round's difference after CleanUp) plus the 7-clubs
+ * bonus, +7 Alex / -7 Bob (eq. final_util). */
+static int final_game_diff(const or_tree *t, int64_t j, int64_t s) {
+    int16_t sc[4];
+    or_final_leaf(slot_score(t, t->root_of[8][j], s), &t->rus[8][7 * j], t->st[8][3 * j + 2], sc);
+    return sc[2] + (sc[3] == 1 ? 7 : (sc[3] == 2 ? -7 : 0));
+}
+
+/*
+ * n_games games from FGT root root_q of rounds[0]; rounds[i+1] is the round after rounds[i],
+ * lnk[i] its leaf-to-next-root links (or_next_roots), and the last round is the final one.
+ * sigma[i]: float strategy of every FGT edge of rounds[i] (levels 1..8 concatenated, FGT order).
+ * At every ply (numbered from 0 across the rounds) the mover's move is drawn as follows, in
+ * float arithmetic: u = sp_uniform(seed, game, ply); with w_a the strategies of the node's
+ * children in canonical order, total = w_0 + w_1 + ... (left to right) and target = u * total,
+ * the move is the first a with w_0 + ... + w_a > target; when there is none (total 0 or a
+ * rounding tie) it is the last a with w_a > 0, else a = 0.  out[g] = final game difference of
+ * game g (Alex minus Bob points of the whole game including the root's inherited difference,
+ * bonus included).  Returns 0, or -1 on invalid arguments.
+ */
+int or_selfplay(const or_tree *const *rounds, int n_rounds, const float *const *sigma, const int64_t *const *lnk,
+                int64_t root_q, int64_t n_games, uint64_t seed, int16_t *out) {
+    if (n_rounds < 1 || !rounds[n_rounds - 1]->final_round) return -1;
+    for (int i = 0; i < n_rounds; i++)
+        if (!rounds[i]->unfolded) return -1;
+    if (root_q < 0 || root_q >= rounds[0]->nq[0]) return -1;
+    for (int64_t g = 0; g < n_games; g++) {
+        int64_t q = root_q, ply = 0;
+        for (int i = 0; i < n_rounds; i++) {
+            const or_tree *t = rounds[i];
+            int64_t j = gt_root_of(t, q), s = q - t->fgt_off[0][j];
+            int64_t base[9] = {0};
+            for (int k = 2; k <= 8; k++) base[k] = base[k - 1] + t->nq[k - 1];
+            for (int k = 0; k < 8; k++) {
+                int d = t->nchild[k][j];
+                int64_t cb = t->child_beg[k][j];
+                float u = sp_uniform(seed, g, ply++);
+                float total = 0.0f;
+                for (int a = 0; a < d; a++) total += sigma[i][base[k + 1] + t->fgt_off[k + 1][cb + a] + s];
+                float target = u * total, cum = 0.0f;
+                int pick = -1, last_pos = -1;
+                for (int a = 0; a < d; a++) {
+                    float w = sigma[i][base[k + 1] + t->fgt_off[k + 1][cb + a] + s];
+                    cum += w;
+                    if (w > 0.0f) last_pos = a;
+                    if (pick < 0 && cum > target) pick = a;
+                }
+                if (pick < 0) pick = last_pos >= 0 ? last_pos : 0;
+                j = cb + pick;
+            }
+            int64_t leaf = t->fgt_off[8][j] + s;
+            if (i + 1 < n_rounds) q = lnk[i][leaf];
+            else out[g] = (int16_t)final_game_diff(t, j, s);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Exact distribution of the final game difference when both players follow sigma (double,
+ * laid out as in or_selfplay) from FGT root root_q: the probability of reaching every FGT node
+ * is carried forward level by level (a child gets its parent's probability times its strategy),
+ * each leaf's probability moves to its linked next-round root, and each final leaf adds its
+ * probability to the bin of its final game difference.  prob[b] = P(difference = lo + b) for
+ * b < n_bins.  Returns 0, or -1 on invalid arguments or a difference outside the bins.
+ */
+int or_outcome_distribution(const or_tree *const *rounds, int n_rounds, const double *const *sigma,
+                            const int64_t *const *lnk, int64_t root_q, int lo, int n_bins, double *prob) {
+    if (n_rounds < 1 || !rounds[n_rounds - 1]->final_round) return -1;
+    for (int b = 0; b < n_bins; b++) prob[b] = 0.0;
+    double *root_p = (double *)calloc((size_t)rounds[0]->nq[0] + 1, sizeof(double));
+    root_p[root_q] = 1.0;
+    int rc = 0;
+    for (int i = 0; i < n_rounds && rc == 0; i++) {
+        const or_tree *t = rounds[i];
+        double *cur = root_p, *next = NULL;
+        int64_t base = 0;
+        for (int k = 0; k < 8; k++) {
+            next = (double *)calloc((size_t)t->nq[k + 1] + 1, sizeof(double));
+            for (int64_t j = 0; j < t->n[k]; j++) {
+                int64_t S = t->fgt_off[k][j + 1] - t->fgt_off[k][j];
+                for (int a = 0; a < t->nchild[k][j]; a++) {
+                    int64_t c = t->child_beg[k][j] + a;
+                    for (int64_t s = 0; s < S; s++) {
+                        int64_t qc = t->fgt_off[k + 1][c] + s;
+                        next[qc] = cur[t->fgt_off[k][j] + s] * sigma[i][base + qc];
+                    }
+                }
+            }
+            base += t->nq[k + 1];
+            free(cur);
+            cur = next;
+        }
+        if (i + 1 < n_rounds) {
+            root_p = (double *)calloc((size_t)rounds[i + 1]->nq[0] + 1, sizeof(double));
+            for (int64_t q = 0; q < t->nq[8]; q++) root_p[lnk[i][q]] += cur[q];
+        } else {
+            for (int64_t j = 0; j < t->n[8]; j++) {
+                int64_t S = t->fgt_off[8][j + 1] - t->fgt_off[8][j];
+                for (int64_t s = 0; s < S; s++) {
+                    double p = cur[t->fgt_off[8][j] + s];
+                    if (p == 0.0) continue;
+                    int b = final_game_diff(t, j, s) - lo;
+                    if (b < 0 || b >= n_bins) { rc = -1; break; }
+                    prob[b] += p;
+                }
+                if (rc) break;
+            }
+        }
+        free(cur);
+    }
+    return rc;
 }
