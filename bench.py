@@ -54,6 +54,22 @@ def mask_of(cards) -> int:
 # GPU path (through the C ABI)
 # ---------------------------------------------------------------------------------------------
 
+SELFPLAY_GAMES = 10000  # self-play games per deal and step
+_DECK_SEEDS: dict = {}
+
+
+def deck_seed(deck) -> int:
+    """Philox key of a deal's self-play: the seed the deal was drawn from."""
+    return _DECK_SEEDS[bytes(np.asarray(deck, np.uint8))]
+
+
+def selfplay_summary(ctx, games):
+    ms, n = ctx.pasur_last_selfplay_stats()
+    g = games.cpu().numpy() if hasattr(games, "cpu") else games
+    return {"games": int(n), "kernel_ms": ms, "alex_win_frac": float((g > 0).mean()), "tie_frac": float((g == 0).mean()),
+            "mean_final_diff": float(g.astype(np.float64).mean())}
+
+
 def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
     """One step.  Returns (node_updates, cfr_kernel_ms, nontrivial_edges_x_T, bytes_h2d, bytes_d2h, trees_info)."""
     cfg = P.pasur_config_default(iters=T)
@@ -91,10 +107,18 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
         outs.append(sb)
         nxt = U
     root_u = float(nxt[0]) if len(nxt) else 0.0
+    # self-play of the solved profile through the rounds (fair value = P(Alex wins))
+    if out_device:
+        games = torch.empty(SELFPLAY_GAMES, dtype=torch.int16, device="cuda")
+    else:
+        games = np.empty(SELFPLAY_GAMES, np.int16)
+        d2h += games.nbytes
+    ctx.pasur_selfplay(trees, SELFPLAY_GAMES, int(deck_seed(deck)), sigmas=None, out=games)
+    sp = selfplay_summary(ctx, games)
     info = [(t.pasur_tree_sizes()[1].tolist()) for t in trees]
     for t in trees:
         t.free()
-    return updates, kms, d2h, h2d, root_u, info
+    return updates, kms, d2h, h2d, root_u, info, sp
 
 
 def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
@@ -123,8 +147,16 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
                 t.pasur_avg_strategy(sb)
             if d == 0:
                 info.append(q.tolist())
+    seeds = np.array([deck_seed(dk) for dk in decks], np.uint64)
+    if out_device:
+        games = torch.empty((len(decks), SELFPLAY_GAMES), dtype=torch.int16, device="cuda")
+    else:
+        games = np.empty((len(decks), SELFPLAY_GAMES), np.int16)
+        d2h += games.nbytes
+    b.pasur_batch_selfplay(SELFPLAY_GAMES, seeds, out=games)
+    sp = selfplay_summary(ctx, games)
     b.free()
-    return edges * T, ms, d2h, decks.nbytes, float(u[0]), info
+    return edges * T, ms, d2h, decks.nbytes + seeds.nbytes, float(u[0]), info, sp
 
 
 class ClockSampler:
@@ -201,9 +233,12 @@ def run_ours(args, rank, world, dist):
     if args.workload == "batch64":
         base = args.seed + rank * BATCH_DEALS
         deck = np.stack([P.pasur_deal(base + i) for i in range(BATCH_DEALS)])
+        for i in range(BATCH_DEALS):
+            _DECK_SEEDS[bytes(deck[i])] = base + i
         solve = solve_batch
     else:
         deck = P.pasur_deal(seed)
+        _DECK_SEEDS[bytes(deck)] = seed
         solve = solve_deal
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -222,7 +257,7 @@ def run_ours(args, rank, world, dist):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            u, kms, _, _, root_u, info = solve(P, ctx, deck, first_round, T, True, torch)
+            u, kms, _, _, root_u, info, sp = solve(P, ctx, deck, first_round, T, True, torch)
             e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -245,7 +280,7 @@ def run_ours(args, rank, world, dist):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, _, d2h, h2d, _, _ = solve(P, ctx, deck, first_round, T, False, torch)
+        _, _, d2h, h2d, _, _, _ = solve(P, ctx, deck, first_round, T, False, torch)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     if dist:
@@ -284,6 +319,8 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches // max(1, args.steps),
         "clocks": clk.summary(),
         "root_utility": root_u,
+        "selfplay": dict(sp, note="games per deal through every solved round, moves drawn from the average "
+                                  "strategy with Philox4x64-10 (key = deal seed); inside each timed step"),
         "wall_s_timed": wall,
     }
     return line

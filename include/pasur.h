@@ -199,6 +199,37 @@ int pasur_batch_tree(const pasur_batch *b, int64_t deal, int round, pasur_tree *
 int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *launches);
 int pasur_batch_free(pasur_batch *b);
 
+/* ---- self-play (fair value) ---------------------------------------------------------------- */
+/* Sampled games: the paper estimates the fair value of a deal by playing many games on the GPU
+ * between strategy profiles (§Introduction, learned-strategy study), every move drawn at the node
+ * reached, one choice per parent (§External Sampling).
+ *
+ * pasur_selfplay plays n_games games from FGT root root_q of rounds[0] through the n_rounds trees
+ * rounds[0..n_rounds) (host array): consecutive rounds of one deal, the last one round 5, each
+ * non-final tree with pasur_next_roots called and the next tree unfolded over exactly the roots
+ * it returned (EINVAL when the sizes disagree).  sigma: NULL or a host array of n_rounds
+ * pointers; entry i NULL uses tree i's average strategy (its CFR run), else the strategy of every
+ * FGT edge of round i in the pasur_avg_strategy layout (float, host or device, read only during
+ * the call).  Move rule, in float arithmetic, at ply p of game g (plies numbered from 0 across the
+ * rounds): u = the top 24 bits of word 0 of Philox4x64-10 (Salmon et al., SC 2011) at counter
+ * (p, g, 0, 0) under key (seed, 0), times 2^-24; w_a = the strategies of the node's children in
+ * canonical order; total = w_0 + w_1 + ... (left to right); the move is the first a with
+ * w_0 + ... + w_a > u * total; if there is none, the last a with w_a > 0, else a = 0.
+ * out: int16 per game (host or device): the final game difference, Alex minus Bob points of the
+ * whole game including root_q's inherited difference and the 7-clubs bonus.  Game g depends only
+ * on (seed, g), not on n_games.  Errors: EINVAL (arguments above, missing CFR run), ENOMEM. */
+int pasur_selfplay(pasur_ctx *ctx, pasur_tree *const *rounds, int n_rounds, const float *const *sigma, int64_t root_q,
+                   int64_t n_games, uint64_t seed, int16_t *out);
+
+/* The same over a solved batch: n_games games per deal from its first round's root with the
+ * batch's average strategies, deal d under seeds[d] (host, n_deals), all deals in one launch.
+ * out: int16 [n_deals * n_games] deal-major, host or device.  EINVAL before pasur_batch_solve. */
+int pasur_batch_selfplay(pasur_batch *b, int64_t n_games, const uint64_t *seeds, int16_t *out);
+
+/* Device time (CUDA events around the self-play kernel) and number of games of the context's last
+ * pasur_selfplay or pasur_batch_selfplay call. */
+int pasur_last_selfplay_stats(const pasur_ctx *ctx, float *ms, int64_t *games);
+
 /* Exclusive prefix sum of per-node move counts into CSR child offsets, allocating nothing.
  * This is the step between the count and emit passes of the level expansion; the paper has no
  * counterpart (its expansion runs on PyTorch tensor ops).  It exists for callers that cannot

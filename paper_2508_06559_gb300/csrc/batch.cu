@@ -304,3 +304,64 @@ int pasur_batch_free(pasur_batch *b) {
 }
 
 }  // extern "C"
+
+extern "C" int pasur_batch_selfplay(pasur_batch *b, int64_t n_games, const uint64_t *seeds, int16_t *out) {
+    if (!b) return PASUR_EINVAL;
+    pasur_ctx *ctx = b->ctx;
+    if (!b->solved) return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: call pasur_batch_solve first");
+    if (n_games < 0 || n_games > ((int64_t)1 << 40) / b->n_deals)
+        return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: n_games out of range");
+    if (n_games > 0 && (!seeds || !out)) return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: NULL seeds or out");
+    cudaSetDevice(ctx->device);
+    if (n_games == 0) {
+        ctx->selfplay_ms = 0.f;
+        ctx->selfplay_games = 0;
+        return PASUR_OK;
+    }
+    std::vector<std::pair<void *, size_t>> tmp;
+    auto alloc = [&](void **p, size_t bytes) {
+        int rc = dev_alloc(ctx, p, bytes);
+        if (rc == PASUR_OK) tmp.push_back({*p, bytes});
+        return rc;
+    };
+    // every tree's average strategy, one buffer, tree after tree
+    std::vector<int64_t> sig_off(b->trees.size() + 1, 0);
+    for (size_t i = 0; i < b->trees.size(); i++) {
+        const pasur_tree *t = b->trees[i];
+        int64_t ne = 0;
+        for (int k = 1; k < 9; k++) ne += t->Q[k];
+        sig_off[i + 1] = sig_off[i] + ne;
+    }
+    float *sig = nullptr;
+    SpRound *views_d = nullptr;
+    uint64_t *seeds_d = nullptr;
+    int64_t *roots_d = nullptr;
+    int16_t *out_d = nullptr;
+    const bool out_dev = is_device_ptr(out);
+    const int64_t total = b->n_deals * n_games;
+    int rc = alloc((void **)&sig, sizeof(float) * (size_t)(sig_off.back() + 1));
+    std::vector<SpRound> views(b->trees.size());
+    for (size_t i = 0; i < b->trees.size() && rc == PASUR_OK; i++) {
+        rc = cfr_export_sigma(b->trees[i], sig + sig_off[i]);
+        selfplay_view(b->trees[i], sig + sig_off[i], &views[i]);
+    }
+    if (rc == PASUR_OK) rc = alloc((void **)&views_d, sizeof(SpRound) * views.size());
+    if (rc == PASUR_OK) rc = alloc((void **)&seeds_d, sizeof(uint64_t) * (size_t)b->n_deals);
+    if (rc == PASUR_OK) rc = alloc((void **)&roots_d, sizeof(int64_t) * (size_t)b->n_deals);
+    if (rc == PASUR_OK && !out_dev) rc = alloc((void **)&out_d, sizeof(int16_t) * (size_t)total);
+    if (rc == PASUR_OK) {
+        if (out_dev) out_d = out;
+        if (cudaMemcpyAsync(views_d, views.data(), sizeof(SpRound) * views.size(), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(seeds_d, seeds, sizeof(uint64_t) * (size_t)b->n_deals, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemsetAsync(roots_d, 0, sizeof(int64_t) * (size_t)b->n_deals, ctx->stream) != cudaSuccess)
+            rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_selfplay: upload");
+    }
+    // the first round of every deal has a single FGT root (index 0)
+    if (rc == PASUR_OK) rc = selfplay_launch(ctx, views_d, b->n_rounds, b->n_deals, n_games, seeds_d, roots_d, out_d);
+    if (rc == PASUR_OK && !out_dev &&
+        cudaMemcpyAsync(out, out_d, sizeof(int16_t) * (size_t)total, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_selfplay: copy results");
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PASUR_OK) rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_selfplay: sync");
+    for (auto &x : tmp) dev_free(ctx, x.first, x.second);
+    return rc;
+}

@@ -226,20 +226,11 @@ __global__ void k_leaf_values(const GTState *__restrict__ st, const int32_t *__r
         int32_t g = root[j];
         int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0;
         if (final_round) {
-            // CleanUp: the last picker of the round takes what is left in the pool
-            uint64_t r = s.rus;
-            int L = rus_get(r, 2);
-            if (L != 0 && s.pool != 0) {
-                int w = L - 1;
-                r = rus_add(r, w, set_clubs(s.pool));
-                r = rus_add(r, 3 + 2 * w, set_points(s.pool));
-            }
+            uint64_t r = cleanup_rus(s.rus, s.pool);
             int d = rus_diff(r);
             for (int64_t x = 0; x < ns; x++) {
                 pasur_score sc = scores[score_off[g] + x];
-                int ac = sc.a_clubs + rus_get(r, 0), bc = sc.b_clubs + rus_get(r, 1), bonus = sc.bonus;
-                normalize_score(ac, bc, bonus);
-                float v = (float)(d + (bonus == 1 ? 7 : (bonus == 2 ? -7 : 0)));
+                float v = (float)(d + bonus_points(bonus_after(sc.a_clubs, sc.b_clubs, sc.bonus, r)));
                 out[q0 + x] = v;
                 local_max = fmaxf(local_max, fabsf(v));
             }

@@ -76,6 +76,27 @@ __host__ __device__ __forceinline__ void normalize_score(int &ac, int &bc, int &
     }
 }
 
+// CleanUp at the end of the final round (caption of Fig. game_0): the last picker takes what is
+// left in the pool with its clubs and points; with no picker in the round the pool is discarded.
+__host__ __device__ __forceinline__ uint64_t cleanup_rus(uint64_t r, uint64_t pool) {
+    int L = rus_get(r, 2);
+    if (L != 0 && pool != 0) {
+        int w = L - 1;
+        r = rus_add(r, w, set_clubs(pool));
+        r = rus_add(r, 3 + 2 * w, set_points(pool));
+    }
+    return r;
+}
+
+// Owner of the 7-clubs bonus (0 none, 1 Alex, 2 Bob) after a round that ends with running score
+// r from the root score (clubs carried, bonus recorded), and its points for Alex (eq. final_util).
+__host__ __device__ __forceinline__ int bonus_after(int a_clubs, int b_clubs, int bonus, uint64_t r) {
+    int ac = a_clubs + rus_get(r, 0), bc = b_clubs + rus_get(r, 1), bn = bonus;
+    normalize_score(ac, bc, bn);
+    return bn;
+}
+__host__ __device__ __forceinline__ int bonus_points(int bonus) { return bonus == 1 ? 7 : (bonus == 2 ? -7 : 0); }
+
 // Sort key of a score: ascending key = lexicographic (a_clubs, b_clubs, delta, bonus), signed.
 __host__ __device__ __forceinline__ uint32_t score_key(int ac, int bc, int delta, int bonus) {
     return ((uint32_t)ac << 22) | ((uint32_t)bc << 18) | ((uint32_t)(delta + 32768) << 2) | (uint32_t)bonus;
@@ -111,6 +132,8 @@ struct pasur_ctx {
     cudaStream_t aux[8] = {nullptr};  // forked streams for concurrent launches (created on first use)
     cudaEvent_t fork = nullptr, join[8] = {nullptr}, cls_t0[8] = {nullptr}, cls_t1[8] = {nullptr};
     int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
+    float selfplay_ms = 0.f;     // device time of the last self-play launch
+    int64_t selfplay_games = 0;  //   and its number of games
 };
 
 struct RootInfo {             // one GT root's subtree, level by level
@@ -293,6 +316,25 @@ int cfr_export_sigma(const pasur_tree *t, float *out_dev);
 int cfr_export_utilities(const pasur_tree *t, float *out_dev);
 int cfr_export_utilities_n(const pasur_tree *t, int64_t iters, float *out_dev);
 int ensure_aux(pasur_ctx *ctx);
+
+// selfplay.cu: device view of one round tree for the self-play kernel
+struct SpRound {
+    const int64_t *child_off[8];   // GT CSR child offsets, levels 0..7
+    const int64_t *fgt_off[9];     // first FGT node of every GT node, levels 0..8
+    const float *sigma;            // strategy per FGT edge, levels 1..8 concatenated
+    int64_t sig_base[9];           // offset of level k in sigma (k >= 1)
+    const int64_t *lnk;            // FGT leaf -> next-round FGT root (non-final rounds)
+    int64_t n_roots;               // GT roots
+    const pasur::GTState *st8;     // final round: leaf states
+    const int32_t *root8;          //   root id of every leaf
+    const int64_t *score_off;      //   score slots of every root
+    const pasur_score *scores;
+};
+void selfplay_view(const pasur_tree *t, const float *sigma_dev, SpRound *v);
+// games of n_deals deals (views[d * n_rounds + i]); seeds_dev / roots_dev per deal; out_dev
+// int16 [n_deals * n_games], deal-major; records the kernel's device time in ctx
+int selfplay_launch(pasur_ctx *ctx, const SpRound *views_dev, int n_rounds, int64_t n_deals, int64_t n_games,
+                    const uint64_t *seeds_dev, const int64_t *roots_dev, int16_t *out_dev);
 
 // between.cu
 int next_roots(pasur_tree *t, std::vector<uint64_t> &pools, std::vector<int64_t> &score_off,

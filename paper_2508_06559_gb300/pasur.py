@@ -28,7 +28,8 @@ EXPORTS = [
     "pasur_build_round", "pasur_tree_free", "pasur_tree_sizes", "pasur_unfold", "pasur_cfr_iterate",
     "pasur_avg_strategy", "pasur_round_utilities", "pasur_next_roots", "pasur_export_level", "pasur_leaf_values",
     "pasur_last_cfr_stats", "pasur_batch_create", "pasur_batch_solve", "pasur_batch_tree", "pasur_batch_stats",
-    "pasur_batch_free", "pasur_move_offsets_noalloc",
+    "pasur_batch_free", "pasur_move_offsets_noalloc", "pasur_selfplay", "pasur_batch_selfplay",
+    "pasur_last_selfplay_stats",
 ]
 
 
@@ -87,6 +88,9 @@ def load() -> C.CDLL:
     L.pasur_batch_tree.argtypes = [vp, i64, C.c_int, C.POINTER(vp)]
     L.pasur_batch_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, i64p]
     L.pasur_batch_free.argtypes = [vp]
+    L.pasur_selfplay.argtypes = [vp, C.POINTER(vp), C.c_int, C.POINTER(vp), i64, i64, C.c_uint64, vp]
+    L.pasur_batch_selfplay.argtypes = [vp, i64, vp, vp]
+    L.pasur_last_selfplay_stats.argtypes = [vp, C.POINTER(C.c_float), i64p]
     for name in EXPORTS:
         if name != "pasur_last_error":
             getattr(L, name).restype = C.c_int
@@ -187,6 +191,34 @@ class Ctx:
         return t
 
 
+    def pasur_selfplay(self, trees, n_games: int, seed: int, root_q: int = 0, sigmas=None, out=None):
+        """Final game differences (int16 per game) of sampled games through consecutive round
+        trees; sigmas: None, or per round None (the tree's average strategy) or a float32 array
+        or tensor per FGT edge."""
+        hs = (vp * len(trees))(*[t.h for t in trees])
+        keep = []
+        sp = None
+        if sigmas is not None:
+            ptrs = []
+            for sg in sigmas:
+                if sg is None:
+                    ptrs.append(None)
+                else:
+                    sg = sg if hasattr(sg, "data_ptr") else np.ascontiguousarray(sg, np.float32)
+                    keep.append(sg)
+                    ptrs.append(_ptr(sg))
+            sp = (vp * len(ptrs))(*ptrs)
+        if out is None:
+            out = np.zeros(n_games, np.int16)
+        _check(load().pasur_selfplay(self.h, hs, len(trees), sp, root_q, n_games, seed, _ptr(out)), self.h)
+        return out
+
+    def pasur_last_selfplay_stats(self):
+        ms, g = C.c_float(0), C.c_int64(0)
+        _check(load().pasur_last_selfplay_stats(self.h, C.byref(ms), C.byref(g)), self.h)
+        return ms.value, g.value
+
+
 class Batch:
     """pasur_batch_create / _solve / _tree / _stats / _free: many deals solved together."""
 
@@ -224,6 +256,15 @@ class Batch:
         ms, e, l = C.c_float(0), C.c_int64(0), C.c_int64(0)
         _check(load().pasur_batch_stats(self.h, C.byref(ms), C.byref(e), C.byref(l)), self.ctx.h)
         return ms.value, e.value, l.value
+
+    def pasur_batch_selfplay(self, n_games: int, seeds, out=None):
+        """n_games games per deal (deal d under seeds[d]); int16 [n_deals, n_games]."""
+        sd = np.ascontiguousarray(seeds, np.uint64)
+        assert sd.shape == (self.n_deals,)
+        if out is None:
+            out = np.zeros((self.n_deals, n_games), np.int16)
+        _check(load().pasur_batch_selfplay(self.h, n_games, _ptr(sd), _ptr(out)), self.ctx.h)
+        return out
 
 
 class Tree:
