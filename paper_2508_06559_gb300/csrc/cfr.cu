@@ -646,13 +646,32 @@ int build_layout(pasur_tree *t) {
 
 }  // namespace
 
+// Largest dynamic shared memory a CFR block may request: the per-block opt-in limit minus the
+// kernel's own static shared memory (largest over its instantiations).
+int cfr_dyn_smem_limit(pasur_ctx *ctx, size_t *limit) {
+    size_t st = 0;
+    cudaFuncAttributes fa;
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<0, 256>));
+    st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<1, 256>));
+    st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<0, 1024>));
+    st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<1, 1024>));
+    st = std::max(st, fa.sharedSizeBytes);
+    *limit = ctx->smem_optin > st ? ctx->smem_optin - st : 0;
+    return PASUR_OK;
+}
+
 int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need) {
     pasur_ctx *ctx = t->ctx;
     PASUR_TRY(build_layout(t));
     // every root goes to the smallest shared-memory class its subtree fits with one slot; its
     // items then take as many slots as that class holds
+    size_t dyn_max = 0;
+    PASUR_TRY(cfr_dyn_smem_limit(ctx, &dyn_max));
     size_t budget[kNumCls - 1];
-    for (int c = 0; c < kNumCls - 1; c++) budget[c] = kClsBudget[c] ? std::min<size_t>(kClsBudget[c], ctx->smem_optin) : ctx->smem_optin;
+    for (int c = 0; c < kNumCls - 1; c++) budget[c] = kClsBudget[c] ? std::min<size_t>(kClsBudget[c], dyn_max) : dyn_max;
     const int wcap = cfg->slots_per_item > 0 ? std::min(cfg->slots_per_item, kMaxSlots) : kMaxSlots;
     int64_t data = 0, scratch = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
@@ -754,11 +773,16 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
     }
     size_t max_sm = 0;
     for (int c = 0; c < kNumCls; c++) max_sm = std::max(max_sm, plan.cls_smem[c]);
-    if (max_sm > 48 * 1024) {
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_sm));
+    if (max_sm > 48 * 1024 && !ctx->cfr_smem_raised) {
+        // the attribute is global per kernel: raise it once to the largest dynamic size any plan
+        // can ask for, so that plans prepared later never lower it under an earlier plan's need
+        size_t lim = 0;
+        PASUR_TRY(cfr_dyn_smem_limit(ctx, &lim));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        ctx->cfr_smem_raised = true;
     }
     for (int c = 0; c < kNumCls; c++) {
         plan.cls_blocks[c] = 0;

@@ -132,6 +132,7 @@ struct pasur_ctx {
     cudaStream_t aux[8] = {nullptr};  // forked streams for concurrent launches (created on first use)
     cudaEvent_t fork = nullptr, join[8] = {nullptr}, cls_t0[8] = {nullptr}, cls_t1[8] = {nullptr};
     int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
+    bool cfr_smem_raised = false;  // CFR kernels' dynamic shared-memory limit raised
     float selfplay_ms = 0.f;     // device time of the last self-play launch
     int64_t selfplay_games = 0;  //   and its number of games
 };

@@ -98,3 +98,18 @@ def test_batch_root_values_match_oracle_chain(ctx):
         _, U5 = o5.cfr(o5.leaf_utilities_final(), T)
         _, U4 = o4.cfr(o4.leaf_utilities_linked(ol, U5), T)
         assert abs(float(u[d]) - U4[0]) < 1e-4, (d, float(u[d]), U4[0])
+
+
+def test_batch_with_subtrees_at_the_shared_memory_limit(ctx):
+    """Seeds 1000..1063 (rounds 4-6) include a root whose subtree needs nearly the whole opt-in
+    shared memory of a block; the class budget must leave room for the kernel's static shared
+    memory.  The batch runs, and one deal equals its per-tree solve."""
+    decks = np.stack([O.deal(s) for s in range(1000, 1064)])
+    cfg = P().pasur_config_default(iters=5)
+    b = P().Batch(ctx, decks, 3, cfg)
+    u = b.pasur_batch_solve()
+    assert np.isfinite(u).all()
+    got = b.pasur_batch_tree(0, 3).pasur_round_utilities()
+    b.free()
+    ref = per_tree_solve(ctx, decks[0], 3, cfg)
+    assert (got == ref[3][0]).all()
