@@ -184,6 +184,15 @@ typedef struct pasur_batch pasur_batch;
 int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const pasur_config *cfg,
                        pasur_batch **out);
 
+/* The surrogate-plus-batched form: rounds first_round..last_round only; the leaves of last_round
+ * (< 5) take their next-round values from the surrogate's predictions for the roots that follow
+ * (pasur_mlp_predict_next, computed here once), so the later rounds are never built.  With
+ * last_round = 5, mlp may be NULL and this is pasur_batch_create.  pasur_batch_selfplay needs
+ * last_round = 5.  (pasur_mlp is declared below.) */
+struct pasur_mlp;
+int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
+                           const pasur_config *cfg, struct pasur_mlp *mlp, pasur_batch **out);
+
 /* Solve the batch from scratch: cfg->iters CFR iterations per round, round 5 first, each round's
  * leaf values from the next round's average root utilities (eq. passuputil).  The first call
  * captures the whole backward sweep into a CUDA graph; every call replays it.  root_util_out
@@ -229,6 +238,75 @@ int pasur_batch_selfplay(pasur_batch *b, int64_t n_games, const uint64_t *seeds,
 /* Device time (CUDA events around the self-play kernel) and number of games of the context's last
  * pasur_selfplay or pasur_batch_selfplay call. */
 int pasur_last_selfplay_stats(const pasur_ctx *ctx, float *ms, int64_t *games);
+
+/* ---- game values under fixed or optimal play (exploitability) ---------------------------- */
+/* fp64 value of every FGT root of a round, from its leaves up: mode 0 minimax (Alex maximises,
+ * Bob minimises), 1 Alex's best response to Bob's strategy, 2 Bob's best response to Alex's, 3 both
+ * following the strategy.  Leaves as in pasur_cfr_iterate: final round = the round's difference
+ * after CleanUp + bonus; other rounds = the round's difference + next_values[lnk(leaf)]
+ * (next_values: double per next-round FGT root, host or device; NULL for the final round).
+ * sigma: strategy of every FGT edge in the pasur_avg_strategy layout (host or device), or NULL to
+ * use the tree's own average strategy; unused in mode 0.  Chaining mode 1 (resp. 2) from round 5
+ * down to round 0 gives the best-response values BR_A >= v >= BR_B of a whole-game profile; its
+ * exploitability is (BR_A - BR_B) / 2.  Expected values are summed child by child in canonical
+ * order (no fused multiply-add).  out: double [FGT roots], host or device. */
+int pasur_root_values(pasur_tree *tree, int mode, const float *sigma, const double *next_values, double *out, int64_t cap);
+
+/* ---- round-start utility surrogate ---------------------------------------------------------- */
+/* A 256-256-256-256-1 network (GELU hidden layers) that predicts the average utility U of a
+ * round-start FGT root, so that a round's leaves can take their next-round values (eq.
+ * passuputil) without the later rounds being built and solved.  The paper's learned part is a
+ * gradient-boosted model of the strategy (§Results); this surrogate is trained on the U values
+ * the exact solver produces and uses the solver as its fallback and judge.  Weights are stored in
+ * f32 (Adam state in f32) and used as bf16 by the tensor-core kernels, which accumulate in f32.
+ *
+ * Input features of a root of round r with pool P and score (ac, bc, delta, bonus), 256 values,
+ * exactly representable in bf16: [52*loc + card] = 1 for every card, loc 0 = Alex (in Alex's
+ * hands of rounds r..5, i.e. deck[4+8i .. 8+8i] for i >= r), 1 = Bob (deck[8+8i .. 12+8i]),
+ * 2 = in P, 3 = out (captured before round r); [208] = ac/8, [209] = bc/8, [210] = delta/32,
+ * [211 + bonus] = 1, [214 + r] = 1; for loc = 0, 1, 2: [220 + 4 loc] = clubs / 8, [221 + 4 loc] =
+ * points / 8 (Aces and Jacks 1, two of clubs 2, ten of diamonds 3), [222 + 4 loc] = Jacks / 4,
+ * [223 + 4 loc] = cards / 32 of that location; [232..255] = 0.
+ * Flat parameter layout (f32, 197,377 values): W0 [256 x 256] (row = output unit), b0 [256],
+ * W1, b1, W2, b2, w3 [256], b3 [1]; y = w3 . h3 + b3, h(l+1) = gelu(W_l h_l + b_l), h0 = x,
+ * gelu(z) = z * Phi(z). */
+typedef struct pasur_mlp pasur_mlp;
+
+/* dataset_capacity: rows of the on-device training set (features bf16 + targets f32).  Weights
+ * are drawn Uniform(-1/16, 1/16) from SplitMix64(seed), biases 0. */
+int pasur_mlp_create(pasur_ctx *ctx, int64_t dataset_capacity, uint64_t seed, pasur_mlp **out);
+int pasur_mlp_free(pasur_mlp *mlp);
+/* Replace / read all parameters (flat layout above; host or device).  Setting resets Adam. */
+int pasur_mlp_set_params(pasur_mlp *mlp, const float *params, int64_t n);
+int pasur_mlp_get_params(const pasur_mlp *mlp, float *params, int64_t cap);
+/* Predictions for n feature rows (x: bf16 bit patterns, row-major [n x 256], host or device;
+ * y_out: float [n], host or device). */
+int pasur_mlp_forward(pasur_mlp *mlp, const uint16_t *x, int64_t n, float *y_out);
+/* Mean squared error over n <= 2^20 rows against targets y and its gradient with respect to every
+ * parameter (flat layout), without updating anything; loss_out / grads_out may be NULL. */
+int pasur_mlp_gradients(pasur_mlp *mlp, const uint16_t *x, const float *y, int64_t n, float *loss_out, float *grads_out);
+/* Append every FGT root of a solved tree (features of its pools and score slots, target = its
+ * average utility) to the training set.  EOVERFLOW beyond the capacity. */
+int pasur_mlp_dataset_add_tree(pasur_mlp *mlp, const pasur_tree *tree);
+/* Append n rows given directly (x: bf16 bit patterns [n x 256], y: float [n]; host or device). */
+int pasur_mlp_dataset_add_rows(pasur_mlp *mlp, const uint16_t *x, const float *y, int64_t n);
+int pasur_mlp_dataset_size(const pasur_mlp *mlp, int64_t *n);
+int pasur_mlp_dataset_export(const pasur_mlp *mlp, int64_t first, int64_t count, uint16_t *x_out, float *y_out);
+int pasur_mlp_dataset_clear(pasur_mlp *mlp);
+/* Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error over the training set:
+ * `epochs` passes, each over a fresh shuffle (SplitMix64(shuffle_seed) Fisher-Yates) in batches
+ * of `batch` rows (a multiple of 128, <= 65536; the last batch may be partial).  One CUDA graph
+ * per epoch.  epoch_loss_out (host, may be NULL): mean batch loss of every epoch. */
+int pasur_mlp_train(pasur_mlp *mlp, int epochs, int64_t batch, float lr, uint64_t shuffle_seed, float *epoch_loss_out);
+/* Predicted U of every next-round FGT root of a non-final tree (after pasur_next_roots), in the
+ * order of pasur_next_roots: pass the result to pasur_cfr_iterate as next_root_util. */
+int pasur_mlp_predict_next(pasur_mlp *mlp, const pasur_tree *tree, float *out, int64_t cap);
+/* Features of arbitrary roots of round `round` of a deal (pools[n_pools], score_offs[n_pools+1],
+ * scores; host) as bf16 rows [score_offs[n_pools] x 256] into x_out (host or device). */
+int pasur_mlp_root_features(pasur_ctx *ctx, const uint8_t deck[52], int round, const uint64_t *pools,
+                            const int64_t *score_offs, const pasur_score *scores, int64_t n_pools, uint16_t *x_out);
+/* Device time of the last pasur_mlp_train call and the Adam steps taken so far. */
+int pasur_mlp_stats(const pasur_mlp *mlp, float *last_train_ms, int64_t *adam_steps);
 
 /* Exclusive prefix sum of per-node move counts into CSR child offsets, allocating nothing.
  * This is the step between the count and emit passes of the level expansion; the paper has no

@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 IN, HID = 256, 256
-N_FEATURES_USED = 220
+N_FEATURES_USED = 232
 
 # flat parameter layout (shared with the C ABI's documented layout)
 SHAPES = [("W0", (HID, IN)), ("b0", (HID,)), ("W1", (HID, HID)), ("b1", (HID,)), ("W2", (HID, HID)),
@@ -63,7 +63,10 @@ def features(deck, rnd: int, pool: int, score) -> np.ndarray:
     (the root's pool set), out (every other card: captured in earlier rounds); feature index
     = 52 * location + card id.
     208, 209: Alex's and Bob's carried club counts / 8;  210: inherited difference / 32;
-    211..213: 7-clubs bonus one-hot (none, Alex, Bob);  214..219: round one-hot;  220..255: 0.
+    211..213: 7-clubs bonus one-hot (none, Alex, Bob);  214..219: round one-hot;
+    220 + 4 * loc + (0, 1, 2, 3) for loc = Alex, Bob, pool: that location's clubs / 8, points / 8
+    (Aces and Jacks 1, two of clubs 2, ten of diamonds 3; Table "Pasur Scoring System"),
+    Jacks / 4 and cards / 32;  232..255: 0.
     """
     x = np.zeros(IN, np.float64)
     deck = [int(c) for c in deck]
@@ -84,6 +87,15 @@ def features(deck, rnd: int, pool: int, score) -> np.ndarray:
     x[210] = delta / 32.0
     x[211 + bonus] = 1.0
     x[214 + rnd] = 1.0
+    for L in range(3):
+        cards = [c for c in range(52) if loc[c] == L]
+        clubs = sum(1 for c in cards if c % 4 == 0)
+        points = sum(1 for c in cards if c < 4 or 40 <= c < 44) + 2 * (4 in cards) + 3 * (37 in cards)
+        jacks = sum(1 for c in cards if 40 <= c < 44)
+        x[220 + 4 * L] = clubs / 8.0
+        x[221 + 4 * L] = points / 8.0
+        x[222 + 4 * L] = jacks / 4.0
+        x[223 + 4 * L] = len(cards) / 32.0
     return x
 
 

@@ -12,7 +12,8 @@
 
 struct pasur_batch {
     pasur_ctx *ctx = nullptr;
-    int first_round = 0, n_rounds = 0;
+    int first_round = 0, last_round = 5, n_rounds = 0;
+    std::vector<float *> cut_util;        // per deal: surrogate values of the roots after last_round
     int64_t n_deals = 0;
     std::vector<pasur_tree *> trees;      // [deal * n_rounds + (round - first_round)]
     std::vector<CfrPlan> plans;           // per round (index round - first_round)
@@ -112,7 +113,8 @@ int record_sweep(pasur_batch *b) {
             PASUR_CUDA(ctx, cudaMemsetAsync(t->R, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
             PASUR_CUDA(ctx, cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
             PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
-            const float *next = ri + 1 < b->n_rounds ? b->util[(size_t)(d * b->n_rounds + ri + 1)] : nullptr;
+            const float *next = ri + 1 < b->n_rounds ? b->util[(size_t)(d * b->n_rounds + ri + 1)]
+                                                     : (b->cut_util.empty() ? nullptr : b->cut_util[(size_t)d]);
             PASUR_TRY(launch_leaf_values(t, next, nullptr));
         }
         PASUR_TRY(cfr_launch_plan(ctx, b->plans[(size_t)ri], &b->cfg, 0, b->dcfr));
@@ -131,17 +133,26 @@ extern "C" {
 
 int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const pasur_config *cfg,
                        pasur_batch **out) {
+    return pasur_batch_create_cut(ctx, decks, n_deals, first_round, 5, cfg, nullptr, out);
+}
+
+int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
+                           const pasur_config *cfg, pasur_mlp *mlp, pasur_batch **out) {
     if (!ctx || !out || !cfg || (n_deals > 0 && !decks)) return ctx ? set_err(ctx, PASUR_EINVAL, "pasur_batch_create: NULL argument") : PASUR_EINVAL;
     *out = nullptr;
     if (n_deals < 1 || n_deals > (1 << 20)) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: n_deals must be 1..2^20");
     if (first_round < 0 || first_round > 5) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: first_round must be 0..5");
+    if (last_round < first_round || last_round > 5)
+        return set_err(ctx, PASUR_EINVAL, "pasur_batch_create_cut: last_round must be first_round..5");
+    if (last_round < 5 && !mlp) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create_cut: a cut before round 5 needs the surrogate");
     if (cfg->iters < 1 || (cfg->variant != 0 && cfg->variant != 1))
         return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: cfg.iters >= 1 and variant 0 or 1 required");
     cudaSetDevice(ctx->device);
     pasur_batch *b = new pasur_batch();
     b->ctx = ctx;
     b->first_round = first_round;
-    b->n_rounds = 6 - first_round;
+    b->last_round = last_round;
+    b->n_rounds = last_round - first_round + 1;
     b->n_deals = n_deals;
     b->cfg = *cfg;
     b->trees.assign((size_t)(n_deals * b->n_rounds), nullptr);
@@ -175,6 +186,16 @@ int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, in
                     rc = pasur_next_roots(t, pools.data(), np, soff.data(), scores.data(), nr, nullptr, &np, &nr);
                 }
             }
+        }
+    }
+    // surrogate values of every deal's roots after the last round
+    if (rc == PASUR_OK && last_round < 5) {
+        b->cut_util.assign((size_t)n_deals, nullptr);
+        for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
+            pasur_tree *t = tree_of(b, d, b->n_rounds - 1);
+            rc = batch_alloc(b, (void **)&b->cut_util[(size_t)d], sizeof(float) * (size_t)(t->n_next_roots + 1));
+            if (rc == PASUR_OK && t->n_next_roots > 0)
+                rc = pasur_mlp_predict_next(mlp, t, b->cut_util[(size_t)d], t->n_next_roots);
         }
     }
     // CFR layouts and one merged plan per round
@@ -281,7 +302,7 @@ int pasur_batch_solve(pasur_batch *b, float *root_util_out, int64_t cap) {
 
 int pasur_batch_tree(const pasur_batch *b, int64_t deal, int round, pasur_tree **tree_out) {
     if (!b || !tree_out) return PASUR_EINVAL;
-    if (deal < 0 || deal >= b->n_deals || round < b->first_round || round > 5)
+    if (deal < 0 || deal >= b->n_deals || round < b->first_round || round > b->last_round)
         return set_err(b->ctx, PASUR_EINVAL, "pasur_batch_tree: deal or round out of range");
     *tree_out = b->trees[(size_t)(deal * b->n_rounds + (round - b->first_round))];
     return PASUR_OK;
@@ -309,6 +330,7 @@ extern "C" int pasur_batch_selfplay(pasur_batch *b, int64_t n_games, const uint6
     if (!b) return PASUR_EINVAL;
     pasur_ctx *ctx = b->ctx;
     if (!b->solved) return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: call pasur_batch_solve first");
+    if (b->last_round != 5) return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: the batch must end with the final round");
     if (n_games < 0 || n_games > ((int64_t)1 << 40) / b->n_deals)
         return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: n_games out of range");
     if (n_games > 0 && (!seeds || !out)) return set_err(ctx, PASUR_EINVAL, "pasur_batch_selfplay: NULL seeds or out");

@@ -29,7 +29,11 @@ EXPORTS = [
     "pasur_avg_strategy", "pasur_round_utilities", "pasur_next_roots", "pasur_export_level", "pasur_leaf_values",
     "pasur_last_cfr_stats", "pasur_batch_create", "pasur_batch_solve", "pasur_batch_tree", "pasur_batch_stats",
     "pasur_batch_free", "pasur_move_offsets_noalloc", "pasur_selfplay", "pasur_batch_selfplay",
-    "pasur_last_selfplay_stats",
+    "pasur_last_selfplay_stats", "pasur_mlp_create", "pasur_mlp_free", "pasur_mlp_set_params", "pasur_mlp_get_params",
+    "pasur_mlp_forward", "pasur_mlp_gradients", "pasur_mlp_dataset_add_tree", "pasur_mlp_dataset_add_rows",
+    "pasur_mlp_dataset_size", "pasur_mlp_dataset_export", "pasur_mlp_dataset_clear", "pasur_mlp_train",
+    "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
+    "pasur_batch_create_cut",
 ]
 
 
@@ -84,6 +88,7 @@ def load() -> C.CDLL:
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
+    L.pasur_batch_create_cut.argtypes = [vp, vp, i64, C.c_int, C.c_int, C.POINTER(pasur_config), vp, C.POINTER(vp)]
     L.pasur_batch_solve.argtypes = [vp, vp, i64]
     L.pasur_batch_tree.argtypes = [vp, i64, C.c_int, C.POINTER(vp)]
     L.pasur_batch_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, i64p]
@@ -91,6 +96,22 @@ def load() -> C.CDLL:
     L.pasur_selfplay.argtypes = [vp, C.POINTER(vp), C.c_int, C.POINTER(vp), i64, i64, C.c_uint64, vp]
     L.pasur_batch_selfplay.argtypes = [vp, i64, vp, vp]
     L.pasur_last_selfplay_stats.argtypes = [vp, C.POINTER(C.c_float), i64p]
+    L.pasur_root_values.argtypes = [vp, C.c_int, vp, vp, vp, i64]
+    L.pasur_mlp_create.argtypes = [vp, i64, C.c_uint64, C.POINTER(vp)]
+    L.pasur_mlp_free.argtypes = [vp]
+    L.pasur_mlp_set_params.argtypes = [vp, vp, i64]
+    L.pasur_mlp_get_params.argtypes = [vp, vp, i64]
+    L.pasur_mlp_forward.argtypes = [vp, vp, i64, vp]
+    L.pasur_mlp_gradients.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.pasur_mlp_dataset_add_tree.argtypes = [vp, vp]
+    L.pasur_mlp_dataset_add_rows.argtypes = [vp, vp, vp, i64]
+    L.pasur_mlp_dataset_size.argtypes = [vp, i64p]
+    L.pasur_mlp_dataset_export.argtypes = [vp, i64, i64, vp, vp]
+    L.pasur_mlp_dataset_clear.argtypes = [vp]
+    L.pasur_mlp_train.argtypes = [vp, C.c_int, i64, C.c_float, C.c_uint64, vp]
+    L.pasur_mlp_predict_next.argtypes = [vp, vp, vp, i64]
+    L.pasur_mlp_root_features.argtypes = [vp, vp, C.c_int, vp, vp, vp, i64, vp]
+    L.pasur_mlp_stats.argtypes = [vp, C.POINTER(C.c_float), i64p]
     for name in EXPORTS:
         if name != "pasur_last_error":
             getattr(L, name).restype = C.c_int
@@ -219,14 +240,133 @@ class Ctx:
         return ms.value, g.value
 
 
+N_MLP_PARAMS = 3 * 256 * 256 + 3 * 256 + 256 + 1
+
+
+class Mlp:
+    """The round-start utility surrogate (pasur_mlp_*).  Feature rows are bf16 bit patterns
+    (uint16 [n, 256])."""
+
+    def __init__(self, ctx: "Ctx", dataset_capacity: int = 0, seed: int = 0):
+        h = vp()
+        _check(load().pasur_mlp_create(ctx.h, dataset_capacity, seed, C.byref(h)), ctx.h)
+        self.ctx, self.h = ctx, h
+        ctx._batches.add(self)
+
+    def free(self):
+        if self.h and self.ctx.h:
+            load().pasur_mlp_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self.ctx.h)
+
+    def set_params(self, flat):
+        f = np.ascontiguousarray(flat, np.float32)
+        self._c(load().pasur_mlp_set_params(self.h, _ptr(f), f.size))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(N_MLP_PARAMS, np.float32)
+        self._c(load().pasur_mlp_get_params(self.h, _ptr(out), out.size))
+        return out
+
+    def forward(self, x, out=None):
+        x = x if hasattr(x, "data_ptr") else np.ascontiguousarray(x, np.uint16)
+        n = x.shape[0]
+        if out is None:
+            out = np.zeros(n, np.float32)
+        self._c(load().pasur_mlp_forward(self.h, _ptr(x), n, _ptr(out)))
+        return out
+
+    def gradients(self, x, y):
+        x = np.ascontiguousarray(x, np.uint16)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(N_MLP_PARAMS, np.float32)
+        self._c(load().pasur_mlp_gradients(self.h, _ptr(x), _ptr(y), len(y), _ptr(loss), _ptr(g)))
+        return float(loss[0]), g
+
+    def dataset_add_tree(self, tree: "Tree"):
+        self._c(load().pasur_mlp_dataset_add_tree(self.h, tree.h))
+
+    def dataset_add_rows(self, x, y):
+        x = x if hasattr(x, "data_ptr") else np.ascontiguousarray(x, np.uint16)
+        y = y if hasattr(y, "data_ptr") else np.ascontiguousarray(y, np.float32)
+        self._c(load().pasur_mlp_dataset_add_rows(self.h, _ptr(x), _ptr(y), x.shape[0]))
+
+    def dataset_size(self) -> int:
+        n = C.c_int64(0)
+        self._c(load().pasur_mlp_dataset_size(self.h, C.byref(n)))
+        return n.value
+
+    def dataset_export(self, first: int = 0, count=None):
+        if count is None:
+            count = self.dataset_size() - first
+        x = np.zeros((count, 256), np.uint16)
+        y = np.zeros(count, np.float32)
+        self._c(load().pasur_mlp_dataset_export(self.h, first, count, _ptr(x), _ptr(y)))
+        return x, y
+
+    def dataset_clear(self):
+        self._c(load().pasur_mlp_dataset_clear(self.h))
+
+    def train(self, epochs: int, batch: int, lr: float, shuffle_seed: int = 0) -> np.ndarray:
+        losses = np.zeros(max(epochs, 1), np.float32)
+        self._c(load().pasur_mlp_train(self.h, epochs, batch, lr, shuffle_seed, _ptr(losses)))
+        return losses[:epochs]
+
+    def predict_next(self, tree: "Tree", out=None):
+        n = tree.n_next_roots()
+        if out is None:
+            out = np.zeros(n, np.float32)
+        cap = out.numel() if hasattr(out, "numel") else len(out)
+        self._c(load().pasur_mlp_predict_next(self.h, tree.h, _ptr(out), cap))
+        return out
+
+    def stats(self):
+        ms, st = C.c_float(0), C.c_int64(0)
+        self._c(load().pasur_mlp_stats(self.h, C.byref(ms), C.byref(st)))
+        return ms.value, st.value
+
+
+def pasur_mlp_root_features(ctx: "Ctx", deck, rnd: int, pools, score_offs, scores) -> np.ndarray:
+    d = np.ascontiguousarray(deck, np.uint8)
+    p = np.ascontiguousarray(pools, np.uint64)
+    so = np.ascontiguousarray(score_offs, np.int64)
+    sc = scores_array(scores)
+    out = np.zeros((int(so[-1]), 256), np.uint16)
+    _check(load().pasur_mlp_root_features(ctx.h, _ptr(d), rnd, _ptr(p), _ptr(so), _ptr(sc), len(p), _ptr(out)), ctx.h)
+    return out
+
+
+def chain_values(trees, mode: int, sigmas=None) -> np.ndarray:
+    """Root values of trees[0] with every round's leaves linked to the next tree's values
+    (trees: consecutive rounds ending with the final one; sigmas: per round or None)."""
+    nxt = None
+    for i in range(len(trees) - 1, -1, -1):
+        nxt = trees[i].pasur_root_values(mode, None if sigmas is None else sigmas[i], nxt)
+    return nxt
+
+
 class Batch:
     """pasur_batch_create / _solve / _tree / _stats / _free: many deals solved together."""
 
-    def __init__(self, ctx: Ctx, decks, first_round: int, cfg: pasur_config):
+    def __init__(self, ctx: Ctx, decks, first_round: int, cfg: pasur_config, last_round: int = 5, mlp=None):
         d = np.ascontiguousarray(np.asarray(decks, np.uint8).reshape(-1, 52))
         h = vp()
-        _check(load().pasur_batch_create(ctx.h, _ptr(d), d.shape[0], first_round, C.byref(cfg), C.byref(h)), ctx.h)
-        self.ctx, self.h, self.n_deals, self.first_round = ctx, h, d.shape[0], first_round
+        if last_round == 5 and mlp is None:
+            rc = load().pasur_batch_create(ctx.h, _ptr(d), d.shape[0], first_round, C.byref(cfg), C.byref(h))
+        else:
+            rc = load().pasur_batch_create_cut(ctx.h, _ptr(d), d.shape[0], first_round, last_round, C.byref(cfg),
+                                               mlp.h if mlp is not None else None, C.byref(h))
+        _check(rc, ctx.h)
+        self.ctx, self.h, self.n_deals, self.first_round, self.last_round = ctx, h, d.shape[0], first_round, last_round
         ctx._batches.add(self)
 
     def free(self):
@@ -339,6 +479,21 @@ class Tree:
         self._c(load().pasur_next_roots(self.h, _ptr(pools), npool.value, _ptr(soff), _ptr(scores), nroot.value,
                                         _ptr(lnk), C.byref(npool), C.byref(nroot)))
         return pools, soff, scores, lnk
+
+    def pasur_root_values(self, mode: int, sigma=None, next_values=None) -> np.ndarray:
+        """fp64 root values: mode 0 minimax, 1 Alex best response, 2 Bob best response, 3 on-policy."""
+        q0 = int(self.pasur_tree_sizes()[1][0])
+        out = np.zeros(q0, np.float64)
+        sg = None if sigma is None else (sigma if hasattr(sigma, "data_ptr") else np.ascontiguousarray(sigma, np.float32))
+        nx = None if next_values is None else (next_values if hasattr(next_values, "data_ptr")
+                                               else np.ascontiguousarray(next_values, np.float64))
+        self._c(load().pasur_root_values(self.h, mode, _ptr(sg), _ptr(nx), _ptr(out), q0))
+        return out
+
+    def n_next_roots(self) -> int:
+        npool, nroot = C.c_int64(0), C.c_int64(0)
+        self._c(load().pasur_next_roots(self.h, None, 0, None, None, 0, None, C.byref(npool), C.byref(nroot)))
+        return nroot.value
 
     def pasur_next_roots_nolinks(self):
         """Next roots without copying the links to the host (they stay on the device)."""

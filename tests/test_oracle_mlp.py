@@ -109,4 +109,11 @@ def test_features_of_real_roots(seed):
                 assert sorted(np.flatnonzero(onehot[0])) == sorted(hands_a)
                 assert x[208] * 8 == sc[s][0] and x[209] * 8 == sc[s][1] and x[210] * 32 == sc[s][2]
                 assert x[211:214].sum() == 1 and x[211 + sc[s][3]] == 1
-                assert x[214 + rnd] == 1 and x[214:220].sum() == 1 and not x[220:].any()
+                assert x[214 + rnd] == 1 and x[214:220].sum() == 1 and not x[232:].any()
+                for L in range(3):
+                    ids = np.flatnonzero(onehot[L])
+                    assert x[223 + 4 * L] * 32 == len(ids)
+                    assert x[220 + 4 * L] * 8 == sum(1 for c in ids if c % 4 == 0)        # clubs
+                    assert x[222 + 4 * L] * 4 == sum(1 for c in ids if c // 4 == 10)      # Jacks
+                    pts = {0: 1, 1: 1, 2: 1, 3: 1, 40: 1, 41: 1, 42: 1, 43: 1, 4: 2, 37: 3}
+                    assert x[221 + 4 * L] * 8 == sum(pts.get(int(c), 0) for c in ids)
