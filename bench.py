@@ -35,7 +35,13 @@ WORKLOADS = {
     "final_round": (5, "final round of one seeded deal as a standalone round, score (0,0,0,0)"),
     "batch64": (3, "64 seeded deals (seeds S..S+63), rounds 4-6 (0-based 3-5) of each from the standalone root, "
                    "solved together: one merged persistent launch per round and size class under a CUDA graph"),
+    "surrogate16": (0, "16 seeded deals (seeds S..S+15): rounds 1-3 (0-based 0-2) solved in one batch with the "
+                       "leaves of round 3 valued by the trained surrogate at the round-4 roots (rounds 4-6 never "
+                       "built), against the exact batched solve of all six rounds"),
 }
+SUR_DEALS = 16
+SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..), rounds 4-6 from the standalone root
+SUR_LABEL_ITERS = 300
 BATCH_DEALS = 64
 METRIC = "CFR node-updates/sec"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
@@ -159,6 +165,109 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
     return edges * T, ms, d2h, decks.nbytes + seeds.nbytes, float(u[0]), info, sp
 
 
+_SUR: dict = {}
+
+
+def no_learning_params(P):
+    """A network whose output is the estimate without learning: +7 / -7 when the 7-clubs bonus is
+    already Alex's / Bob's, else 0."""
+    p = np.zeros(P.N_MLP_PARAMS, np.float32)
+    per = 256 * 256 + 256
+    p[0:65536].reshape(256, 256)[0, 212] = 10
+    p[0:65536].reshape(256, 256)[1, 213] = 10
+    for l in (1, 2):
+        W = p[l * per:l * per + 65536].reshape(256, 256)
+        W[0, 0], W[1, 1] = 1, 1
+    p[3 * per], p[3 * per + 1] = 0.7, -0.7
+    return p
+
+
+def surrogate_setup(P, ctx, decks, T, torch):
+    """Untimed: train the surrogate on exact solves of other deals, solve the bench deals exactly
+    (batched, all six rounds, timed for the speedup), and measure the exploitability of the exact,
+    surrogate and no-learning profiles with the fp64 best-response chain."""
+    t0 = time.perf_counter()
+    mlp = P.Mlp(ctx, dataset_capacity=2_000_000, seed=7)
+    cfg_l = P.pasur_config_default(iters=SUR_LABEL_ITERS)
+    for i in range(0, SUR_TRAIN_DEALS, 64):
+        b = P.Batch(ctx, np.stack([P.pasur_deal(10000 + i + j) for j in range(64)]), 3, cfg_l)
+        b.pasur_batch_solve()
+        for d in range(64):
+            for r in (3, 4, 5):
+                mlp.dataset_add_tree(b.pasur_batch_tree(d, r))
+        b.free()
+    gen_s = time.perf_counter() - t0
+    losses = mlp.train(5, 1024, 1e-3, shuffle_seed=1)
+    train_ms, steps = mlp.stats()
+    none = P.Mlp(ctx)
+    none.set_params(no_learning_params(P))
+    cfg = P.pasur_config_default(iters=T)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    be = P.Batch(ctx, decks, 0, cfg)
+    be.pasur_batch_solve()
+    torch.cuda.synchronize()
+    exact_s = time.perf_counter() - t1
+    _, exact_edges, _ = be.pasur_batch_stats()
+    res = {"exact": [], "surrogate": [], "no_learning": [], "mse_surrogate": [], "mse_no_learning": []}
+    cuts = {}
+    for key, net in (("surrogate", mlp), ("no_learning", none)):
+        bs = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
+        bs.pasur_batch_solve()
+        cuts[key] = bs
+    for d in range(len(decks)):
+        te = [be.pasur_batch_tree(d, r) for r in range(6)]
+        res["exact"].append((P.chain_values(te, 1)[0] - P.chain_values(te, 2)[0]) / 2)
+        u3 = te[3].pasur_round_utilities()
+        for key, net in (("surrogate", mlp), ("no_learning", none)):
+            ts = [cuts[key].pasur_batch_tree(d, r) for r in range(3)]
+            sig = [t.pasur_avg_strategy() for t in ts] + [None] * 3
+            res[key].append((P.chain_values(te, 1, sig)[0] - P.chain_values(te, 2, sig)[0]) / 2)
+            res["mse_" + key].append(float(((net.predict_next(ts[2]) - u3) ** 2).mean()))
+    for bs in cuts.values():
+        bs.free()
+    be.free()
+    none.free()
+    _SUR.update(mlp=mlp, info={
+        "train_deals": SUR_TRAIN_DEALS, "train_rows": mlp.dataset_size(), "label_iters": SUR_LABEL_ITERS,
+        "data_gen_s": gen_s, "train_ms": train_ms, "adam_steps": steps, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+        "exact_batch_s": exact_s, "exact_node_updates": exact_edges * T,
+        "exploitability_mean": {k: float(np.mean(res[k])) for k in ("exact", "surrogate", "no_learning")},
+        "exploitability_per_deal": {k: [round(float(x), 4) for x in res[k]] for k in ("exact", "surrogate", "no_learning")},
+        "round4_root_mse": {"surrogate": float(np.mean(res["mse_surrogate"])), "no_learning": float(np.mean(res["mse_no_learning"]))},
+        "target_gap": 1e-3})
+
+
+def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
+    """One step of the surrogate workload: build rounds 0-2 of every deal, value the round-2 leaves
+    with the surrogate at the round-3 roots, solve the three rounds batched, write out."""
+    cfg = P.pasur_config_default(iters=T)
+    b = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=_SUR["mlp"])
+    u = b.pasur_batch_solve()
+    ms, edges, _ = b.pasur_batch_stats()
+    d2h = 0
+    info = []
+    for d in range(len(decks)):
+        for r in range(0, 3):
+            t = b.pasur_batch_tree(d, r)
+            q = t.pasur_tree_sizes()[1]
+            ne = int(q[1:].sum())
+            if out_device:
+                U = torch.empty(int(q[0]), dtype=torch.float32, device="cuda")
+                sb = torch.empty(max(ne, 1), dtype=torch.float32, device="cuda")
+            else:
+                U = np.empty(int(q[0]), np.float32)
+                sb = np.empty(max(ne, 1), np.float32)
+                d2h += U.nbytes + sb.nbytes
+            t.pasur_round_utilities(U)
+            if ne:
+                t.pasur_avg_strategy(sb)
+            if d == 0:
+                info.append(q.tolist())
+    b.free()
+    return edges * T, ms, d2h, decks.nbytes, float(u[0]), info, None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -230,7 +339,12 @@ def run_ours(args, rank, world, dist):
     first_round, desc = WORKLOADS[args.workload]
     seed = args.seed + rank
     T = args.iters
-    if args.workload == "batch64":
+    if args.workload == "surrogate16":
+        base = args.seed + rank * SUR_DEALS
+        deck = np.stack([P.pasur_deal(base + i) for i in range(SUR_DEALS)])
+        solve = solve_surrogate
+        surrogate_setup(P, ctx, deck, T, torch)
+    elif args.workload == "batch64":
         base = args.seed + rank * BATCH_DEALS
         deck = np.stack([P.pasur_deal(base + i) for i in range(BATCH_DEALS)])
         for i in range(BATCH_DEALS):
@@ -319,10 +433,20 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches // max(1, args.steps),
         "clocks": clk.summary(),
         "root_utility": root_u,
-        "selfplay": dict(sp, note="games per deal through every solved round, moves drawn from the average "
-                                  "strategy with Philox4x64-10 (key = deal seed); inside each timed step"),
+        "selfplay": None if sp is None else dict(
+            sp, note="games per deal through every solved round, moves drawn from the average "
+                     "strategy with Philox4x64-10 (key = deal seed); inside each timed step"),
         "wall_s_timed": wall,
     }
+    if args.workload == "surrogate16":
+        si = dict(_SUR["info"])
+        si["surrogate_step_s"] = ms_per_step / 1e3
+        si["speedup_vs_exact"] = si["exact_batch_s"] / (ms_per_step / 1e3)
+        si["gap_vs_exact"] = si["exploitability_mean"]["surrogate"] - si["exploitability_mean"]["exact"]
+        si["note"] = ("exploitability = (BR_Alex - BR_Bob) / 2 of the whole-game profile (rounds 1-3 from the "
+                      "solve under test, rounds 4-6 exact), fp64 best-response chain over all six exact rounds; "
+                      "the speedup compares whole create+solve wall times of the two batched forms")
+        line["surrogate"] = si
     return line
 
 
