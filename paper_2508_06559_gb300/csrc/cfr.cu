@@ -47,69 +47,79 @@ struct CfrParams {
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// shared memory of a resident item: packed active entries (8 B each) and R, S, V, X per
+// (local node, slot); resident items must have fewer than 65535 local nodes
 __host__ __device__ __forceinline__ size_t resident_bytes(int64_t L, int64_t nA, int64_t W) {
-    return 3 * al16((size_t)nA * 4) + al16((size_t)nA * 2) + 4 * al16((size_t)L * W * 4);
+    return L >= 65535 ? ~(size_t)0 >> 1 : 2 * al16((size_t)nA * 4) + 4 * al16((size_t)L * W * 4);
 }
 
 constexpr int KC = 8;  // degrees with a fully unrolled path (larger degrees loop over memory)
 constexpr int kMaxSlots = 32;  // score slots per work item
 
+// Index of child edge a of a node whose first child is local node c, at slot w of an item of W
+// slots (slot-minor layout); W1: single-slot items, where this is c + a.
+template <bool W1>
+__device__ __forceinline__ int at(int c, int a, int W, int w) {
+    return W1 ? c + a : (c + a) * W + w;
+}
+
 // Regret matching at one (active node, slot) with D children and the reach of the children.
 // X[n] holds the reach of the player who moved into node n; own = the mover's reach at the node.
-template <int D>
+template <int D, bool W1>
 __device__ __forceinline__ void td_node(int c, int W, int w, float own, const float *__restrict__ R, float *__restrict__ X,
                                         float thr) {
     if (D == 1) {
-        X[c * W + w] = own;
+        X[at<W1>(c, 0, W, w)] = own;
         return;
     }
     float r[D];
 #pragma unroll
-    for (int a = 0; a < D; a++) r[a] = R[(c + a) * W + w];
+    for (int a = 0; a < D; a++) r[a] = R[at<W1>(c, a, W, w)];
     float sum = 0.f;
 #pragma unroll
     for (int a = 0; a < D; a++) sum += r[a] > thr ? r[a] : 0.f;
     if (sum > 0.f) {
         const float inv = 1.f / sum;
 #pragma unroll
-        for (int a = 0; a < D; a++) X[(c + a) * W + w] = r[a] > thr ? own * (r[a] * inv) : 0.f;
+        for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = r[a] > thr ? own * (r[a] * inv) : 0.f;
     } else {
         const float u = own * (1.f / (float)D);
 #pragma unroll
-        for (int a = 0; a < D; a++) X[(c + a) * W + w] = u;
+        for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = u;
     }
 }
 
+template <bool W1>
 __device__ __forceinline__ void td_node_any(int c, int d, int W, int w, float own, const float *__restrict__ R,
                                             float *__restrict__ X, float thr) {
     float sum = 0.f;
     for (int a = 0; a < d; a++) {
-        const float r = R[(c + a) * W + w];
+        const float r = R[at<W1>(c, a, W, w)];
         sum += r > thr ? r : 0.f;
     }
     if (sum > 0.f) {
         const float inv = 1.f / sum;
         for (int a = 0; a < d; a++) {
-            const float r = R[(c + a) * W + w];
-            X[(c + a) * W + w] = r > thr ? own * (r * inv) : 0.f;
+            const float r = R[at<W1>(c, a, W, w)];
+            X[at<W1>(c, a, W, w)] = r > thr ? own * (r * inv) : 0.f;
         }
     } else {
         const float u = own * (1.f / (float)d);
-        for (int a = 0; a < d; a++) X[(c + a) * W + w] = u;
+        for (int a = 0; a < d; a++) X[at<W1>(c, a, W, w)] = u;
     }
 }
 
 // Value of one (active node, slot) with D children, then R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h))
 // and S(h,a) += pi_p(h) sigma(h,a) for its child edges.  Returns v(h).
-template <int VARIANT, int D>
+template <int VARIANT, int D, bool W1>
 __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float spo, float *__restrict__ R,
                                          float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
                                          float fneg, float fs) {
     float r[D], v[D];
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        r[a] = R[(c + a) * W + w];
-        v[a] = V[(c + a) * W + w];
+        r[a] = R[at<W1>(c, a, W, w)];
+        v[a] = V[at<W1>(c, a, W, w)];
     }
     float sum = 0.f;
 #pragma unroll
@@ -120,7 +130,7 @@ __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float sp
     for (int a = 1; a < D; a++) vh += (sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u) * (v[a] - v[0]);
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        const int q = (c + a) * W + w;
+        const int q = at<W1>(c, a, W, w);
         const float sg = sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u;
         const float inst = spo * (v[a] - vh);
         if (VARIANT == 1) {
@@ -134,24 +144,24 @@ __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float sp
     return vh;
 }
 
-template <int VARIANT>
+template <int VARIANT, bool W1>
 __device__ __forceinline__ float bu_node_any(int c, int d, int W, int w, float pp, float spo, float *__restrict__ R,
                                              float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
                                              float fneg, float fs) {
     float sum = 0.f;
     for (int a = 0; a < d; a++) {
-        const float r = R[(c + a) * W + w];
+        const float r = R[at<W1>(c, a, W, w)];
         sum += r > thr ? r : 0.f;
     }
     const float inv = sum > 0.f ? 1.f / sum : 0.f, u = 1.f / (float)d;
-    const float v0 = V[c * W + w];
+    const float v0 = V[at<W1>(c, 0, W, w)];
     float vh = v0;
     for (int a = 1; a < d; a++) {
-        const float r = R[(c + a) * W + w];
-        vh += (sum > 0.f ? (r > thr ? r * inv : 0.f) : u) * (V[(c + a) * W + w] - v0);
+        const float r = R[at<W1>(c, a, W, w)];
+        vh += (sum > 0.f ? (r > thr ? r * inv : 0.f) : u) * (V[at<W1>(c, a, W, w)] - v0);
     }
     for (int a = 0; a < d; a++) {
-        const int q = (c + a) * W + w;
+        const int q = at<W1>(c, a, W, w);
         const float r = R[q];
         const float sg = sum > 0.f ? (r > thr ? r * inv : 0.f) : u;
         const float inst = spo * (V[q] - vh);
@@ -166,106 +176,177 @@ __device__ __forceinline__ float bu_node_any(int c, int d, int W, int w, float p
     return vh;
 }
 
+// Active entries of an item.  Resident items keep them packed in shared memory, two 32-bit words
+// per entry: (first child | moves << 16) and (local index | parent's local index << 16, 0xFFFF
+// at the root); resident items have fewer than 65535 local nodes.  Items in device memory read
+// the four int arrays.
+template <bool PACKED>
+struct Entries {
+    const uint32_t *cd, *lp;
+    const int32_t *li, *pl, *cs;
+    const uint16_t *d;
+    __device__ __forceinline__ void child(int e, int &c, int &n) const {
+        if (PACKED) {
+            const uint32_t u = cd[e];
+            c = (int)(u & 0xFFFFu);
+            n = (int)(u >> 16);
+        } else {
+            c = cs[e];
+            n = d[e];
+        }
+    }
+    __device__ __forceinline__ void self(int e, int &l, int &p) const {
+        if (PACKED) {
+            const uint32_t u = lp[e];
+            l = (int)(u & 0xFFFFu);
+            p = (u >> 16) == 0xFFFFu ? -1 : (int)(u >> 16);
+        } else {
+            l = li[e];
+            p = pl[e];
+        }
+    }
+};
+
 // One level of the top-down pass over (active node, slot) pairs.  The active entries of a level
 // are sorted by degree, so the lanes of a warp mostly take the same unrolled path.
-template <int VARIANT>
-__device__ __forceinline__ void td_level(int b, int n, int W, int t0x, int stride, const int32_t *__restrict__ Apl,
-                                         const int32_t *__restrict__ Acs, const uint16_t *__restrict__ Ad,
+template <int VARIANT, bool W1, bool PACKED>
+__device__ __forceinline__ void td_level(int b, int n, int W, int t0x, int stride, const Entries<PACKED> &A,
                                          const float *__restrict__ R, float *__restrict__ X, const float *tu, float tf) {
+    const float thr1 = tu[0] * tf;
     for (int x = t0x; x < n; x += stride) {
-        const int e = W == 1 ? b + x : b + x / W, w = W == 1 ? 0 : x % W;
-        const int pl = Apl[e], c = Acs[e], d = Ad[e];
-        const float thr = tu[w] * tf;
-        const float own = pl < 0 ? 1.f : X[pl * W + w];
+        const int e = W1 ? b + x : b + x / W, w = W1 ? 0 : x % W;
+        int c, d, li, pl;
+        A.child(e, c, d);
+        A.self(e, li, pl);
+        const float thr = W1 ? thr1 : tu[w] * tf;
+        const float own = pl < 0 ? 1.f : X[W1 ? pl : pl * W + w];
         switch (d) {
-            case 1: td_node<1>(c, W, w, own, R, X, thr); break;
-            case 2: td_node<2>(c, W, w, own, R, X, thr); break;
-            case 3: td_node<3>(c, W, w, own, R, X, thr); break;
-            case 4: td_node<4>(c, W, w, own, R, X, thr); break;
-            case 5: td_node<5>(c, W, w, own, R, X, thr); break;
-            case 6: td_node<6>(c, W, w, own, R, X, thr); break;
-            case 7: td_node<7>(c, W, w, own, R, X, thr); break;
-            case 8: td_node<8>(c, W, w, own, R, X, thr); break;
-            default: td_node_any(c, d, W, w, own, R, X, thr);
+            case 1: td_node<1, W1>(c, W, w, own, R, X, thr); break;
+            case 2: td_node<2, W1>(c, W, w, own, R, X, thr); break;
+            case 3: td_node<3, W1>(c, W, w, own, R, X, thr); break;
+            case 4: td_node<4, W1>(c, W, w, own, R, X, thr); break;
+            case 5: td_node<5, W1>(c, W, w, own, R, X, thr); break;
+            case 6: td_node<6, W1>(c, W, w, own, R, X, thr); break;
+            case 7: td_node<7, W1>(c, W, w, own, R, X, thr); break;
+            case 8: td_node<8, W1>(c, W, w, own, R, X, thr); break;
+            default: td_node_any<W1>(c, d, W, w, own, R, X, thr);
         }
     }
 }
 
 // One level of the bottom-up pass over (active node, slot) pairs.
-template <int VARIANT>
-__device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int t0x, int stride,
-                                         const int32_t *__restrict__ Ali, const int32_t *__restrict__ Apl,
-                                         const int32_t *__restrict__ Acs, const uint16_t *__restrict__ Ad,
+template <int VARIANT, bool W1, bool PACKED>
+__device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int t0x, int stride, const Entries<PACKED> &A,
                                          float *__restrict__ R, float *__restrict__ S, float *__restrict__ V,
                                          const float *__restrict__ X, const float *tu, float tf, float fpos, float fneg,
                                          float fs) {
+    const float thr1 = tu[0] * tf;
     for (int x = t0x; x < n; x += stride) {
-        const int e = W == 1 ? b + x : b + x / W, w = W == 1 ? 0 : x % W;
-        const int li = Ali[e], pl = Apl[e], c = Acs[e], d = Ad[e];
-        const float thr = tu[w] * tf;
-        const float pp = pl < 0 ? 1.f : X[pl * W + w];  // pi_p(h)
-        const float po = X[li * W + w];                  // pi_{-p}(h)
+        const int e = W1 ? b + x : b + x / W, w = W1 ? 0 : x % W;
+        int c, d, li, pl;
+        A.child(e, c, d);
+        A.self(e, li, pl);
+        const float thr = W1 ? thr1 : tu[w] * tf;
+        const float pp = pl < 0 ? 1.f : X[W1 ? pl : pl * W + w];  // pi_p(h)
+        const float po = X[W1 ? li : li * W + w];                 // pi_{-p}(h)
         const float spo = alex ? po : -po;
         float vh;
         switch (d) {
-            case 1: vh = bu_node<VARIANT, 1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 2: vh = bu_node<VARIANT, 2>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 3: vh = bu_node<VARIANT, 3>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 4: vh = bu_node<VARIANT, 4>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 5: vh = bu_node<VARIANT, 5>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 6: vh = bu_node<VARIANT, 6>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 7: vh = bu_node<VARIANT, 7>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 8: vh = bu_node<VARIANT, 8>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            default: vh = bu_node_any<VARIANT>(c, d, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
+            case 1: vh = bu_node<VARIANT, 1, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 2: vh = bu_node<VARIANT, 2, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 3: vh = bu_node<VARIANT, 3, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 4: vh = bu_node<VARIANT, 4, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 5: vh = bu_node<VARIANT, 5, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 6: vh = bu_node<VARIANT, 6, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 7: vh = bu_node<VARIANT, 7, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 8: vh = bu_node<VARIANT, 8, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            default: vh = bu_node_any<VARIANT, W1>(c, d, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
         }
-        V[li * W + w] = vh;
+        V[W1 ? li : li * W + w] = vh;
     }
+}
+
+// The T iterations of one item over its level schedule: sched[i] for i < 7 the top-down levels
+// 0..6, for i >= 7 the bottom-up levels 7..0; each (first entry, pairs, flags: 1 = empty, 2 = at
+// most 32 pairs (warp 0 alone), 4 = the next non-empty level is also small (a warp barrier
+// suffices)).
+template <int VARIANT, bool W1, bool PACKED>
+__device__ __forceinline__ double iterate(const CfrParams &p, int W, const Entries<PACKED> &A, float *R, float *S,
+                                          float *V, float *X, const int32_t *sb, const int32_t *sn, const int32_t *sf,
+                                          const float *s_tu) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const bool warp0 = tid < 32;
+    double acc = 0.0;
+    for (int il = 0; il < p.iters; il++) {
+        const int64_t t = p.t0 + il + 1;
+        const float tf = (float)t;
+        float fpos = 0.f, fneg = 0.f, fs = 0.f;
+        if (VARIANT == 1) {
+            fpos = p.dcfr[3 * il];
+            fneg = p.dcfr[3 * il + 1];
+            fs = p.dcfr[3 * il + 2];
+        }
+        for (int i = 0; i < 7; i++) {
+            const int f = sf[i];
+            if (f & 1) continue;
+            if (!(f & 2)) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, tid, nth, A, R, X, s_tu, tf);
+            else if (warp0) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, tid, 32, A, R, X, s_tu, tf);
+            if (f & 4) __syncwarp();
+            else __syncthreads();
+        }
+        for (int i = 7; i < 15; i++) {
+            const int f = sf[i];
+            if (f & 1) continue;
+            const bool alex = ((14 - i) & 1) == 0;
+            if (!(f & 2)) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, tid, nth, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+            else if (warp0) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, tid, 32, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+            if (f & 4) __syncwarp();
+            else __syncthreads();
+        }
+        if (tid < W) acc += (double)V[tid];
+        __syncthreads();
+    }
+    return acc;
 }
 
 // All T iterations of one item.  RES: the item's arrays are in shared memory (carved from sm);
 // otherwise they are in device memory.
 template <int VARIANT, bool RES>
 __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv, const CfrItem &it, const CfrRoot &cr,
-                                         const int32_t *s_as, float *s_tu, unsigned char *sm) {
+                                         const int32_t *s_as, float *s_tu, int32_t *sb, int32_t *sn, int32_t *sf,
+                                         unsigned char *sm) {
     const int tid = threadIdx.x, nth = blockDim.x;
-    const bool warp0 = tid < 32;
     const int W = it.ns;
     const int L = cr.ls[9], nA = s_as[9];
-    const int32_t *Ali, *Apl, *Acs;
-    const uint16_t *Ad;
     float *R, *S, *V, *X;
     const int32_t *gli = tv.act_li + cr.act_off, *gpl = tv.act_pl + cr.act_off, *gcs = tv.act_cs + cr.act_off;
     const uint16_t *gd = tv.act_d + cr.act_off;
+    Entries<true> P{};
+    Entries<false> G{};
     if (RES) {
         size_t o = 0;
-        int32_t *sli = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
-        int32_t *spl = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
-        int32_t *scs = (int32_t *)(sm + o); o += al16((size_t)nA * 4);
-        uint16_t *sd = (uint16_t *)(sm + o); o += al16((size_t)nA * 2);
+        uint32_t *scd = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
+        uint32_t *slp = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
         R = (float *)(sm + o); o += al16((size_t)L * W * 4);
         S = (float *)(sm + o); o += al16((size_t)L * W * 4);
         V = (float *)(sm + o); o += al16((size_t)L * W * 4);
         X = (float *)(sm + o);
         for (int i = tid; i < nA; i += nth) {
-            sli[i] = gli[i];
-            spl[i] = gpl[i];
-            scs[i] = gcs[i];
-            sd[i] = gd[i];
+            scd[i] = (uint32_t)gcs[i] | ((uint32_t)gd[i] << 16);
+            slp[i] = (uint32_t)gli[i] | ((uint32_t)(gpl[i] < 0 ? 0xFFFF : gpl[i]) << 16);
         }
         const float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
         for (int i = tid; i < L * W; i += nth) {
             R[i] = gR[i];
             S[i] = gS[i];
         }
-        Ali = sli;
-        Apl = spl;
-        Acs = scs;
-        Ad = sd;
+        P.cd = scd;
+        P.lp = slp;
     } else {
-        Ali = gli;
-        Apl = gpl;
-        Acs = gcs;
-        Ad = gd;
+        G.li = gli;
+        G.pl = gpl;
+        G.cs = gcs;
+        G.d = gd;
         R = tv.R + it.data_base;
         S = tv.S + it.data_base;
         V = tv.V + it.scratch_base;
@@ -288,49 +369,33 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv,
         }
         for (int w = tid; w < W; w += nth) X[w] = 1.f;
     }
+    // level schedule: a level of at most 32 (node, slot) pairs runs on warp 0 alone, and only a
+    // change between warp-0 and whole-block levels needs a block barrier
+    if (tid == 0) {
+        for (int i = 0; i < 15; i++) {
+            const int k = i < 7 ? i : 14 - i;
+            sb[i] = s_as[k];
+            sn[i] = (s_as[k + 1] - s_as[k]) * W;
+        }
+        for (int i = 0; i < 15; i++) {
+            int f = sn[i] == 0 ? 1 : 0;
+            const bool small = sn[i] <= 32;
+            if (small) f |= 2;
+            // next non-empty level in execution order within the same pass
+            const int end = i < 7 ? 7 : 15;
+            int j = i + 1;
+            while (j < end && sn[j] == 0) j++;
+            if (small && j < end && sn[j] <= 32) f |= 4;
+            sf[i] = f;
+        }
+    }
     __syncthreads();
     for (int w = tid; w < W; w += nth) s_tu[w] = p.tau * s_tu[w];
     __syncthreads();
-    double acc = 0.0;
-    for (int il = 0; il < p.iters; il++) {
-        const int64_t t = p.t0 + il + 1;
-        const float tf = (float)t;
-        float fpos = 0.f, fneg = 0.f, fs = 0.f;
-        if (VARIANT == 1) {
-            fpos = p.dcfr[3 * il];
-            fneg = p.dcfr[3 * il + 1];
-            fs = p.dcfr[3 * il + 2];
-        }
-        // top-down over levels 0..6; a level of at most 32 (node, slot) pairs runs on warp 0
-        // alone, and only a change between warp-0 and whole-block levels needs a block barrier
-        for (int k = 0; k < 7; k++) {
-            const int b = s_as[k], n = (s_as[k + 1] - b) * W;
-            if (n == 0) continue;
-            const bool small = n <= 32;
-            if (!small) td_level<VARIANT>(b, n, W, tid, nth, Apl, Acs, Ad, R, X, s_tu, tf);
-            else if (warp0) td_level<VARIANT>(b, n, W, tid, 32, Apl, Acs, Ad, R, X, s_tu, tf);
-            int kn = k + 1;
-            while (kn < 7 && s_as[kn + 1] == s_as[kn]) kn++;
-            const bool next_small = kn < 7 && (s_as[kn + 1] - s_as[kn]) * W <= 32;
-            if (small && next_small) __syncwarp();
-            else __syncthreads();
-        }
-        // bottom-up over levels 7..0
-        for (int k = 7; k >= 0; k--) {
-            const int b = s_as[k], n = (s_as[k + 1] - b) * W;
-            if (n == 0) continue;
-            const bool small = n <= 32, alex = (k & 1) == 0;
-            if (!small) bu_level<VARIANT>(alex, b, n, W, tid, nth, Ali, Apl, Acs, Ad, R, S, V, X, s_tu, tf, fpos, fneg, fs);
-            else if (warp0) bu_level<VARIANT>(alex, b, n, W, tid, 32, Ali, Apl, Acs, Ad, R, S, V, X, s_tu, tf, fpos, fneg, fs);
-            int kn = k - 1;
-            while (kn >= 0 && s_as[kn + 1] == s_as[kn]) kn--;
-            const bool next_small = kn >= 0 && (s_as[kn + 1] - s_as[kn]) * W <= 32;
-            if (small && next_small) __syncwarp();
-            else __syncthreads();
-        }
-        if (tid < W) acc += (double)V[tid];
-        __syncthreads();
-    }
+    double acc;
+    if (RES && W == 1) acc = iterate<VARIANT, true, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu);
+    else if (RES) acc = iterate<VARIANT, false, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu);
+    else acc = iterate<VARIANT, false, false>(p, W, G, R, S, V, X, sb, sn, sf, s_tu);
     if (tid < W) {
         if (!isfinite(acc)) atomicOr(p.err, 1);
         tv.uacc[tv.fgt_off0[it.root] + it.s0 + tid] += acc;
@@ -346,10 +411,11 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv,
 }
 
 template <int VARIANT, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_cfr_items(CfrParams p) {
+__global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrParams p) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_item;
     __shared__ int32_t s_as[10];
+    __shared__ int32_t s_sb[15], s_sn[15], s_sf[15];
     __shared__ float s_tu[kMaxSlots];
     const int tid = threadIdx.x;
     for (;;) {
@@ -362,8 +428,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_cfr_items(CfrParams p) {
         const CfrItem it = p.items[id];
         const TreeView tv = p.views[it.tree];
         const CfrRoot &cr = tv.roots[it.root];
-        if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, sm);
-        else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, sm);
+        if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
+        else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
     }
 }
 
@@ -708,6 +774,9 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
                 need[cls] = std::max(need[cls], resident_bytes(L, nA, it.ns));
             }
             it.cost = std::max<int64_t>(nA, 1) * it.ns;
+            int32_t wmax = 0;
+            for (int k = 0; k < 8; k++) wmax = std::max<int32_t>(wmax, (cr.as[k + 1] - cr.as[k]) * it.ns);
+            it.width = wmax;
             cls_items[cls].push_back(it);
         }
     }
@@ -786,9 +855,18 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
     }
     for (int c = 0; c < kNumCls; c++) {
         plan.cls_blocks[c] = 0;
-        const int threads = cfg->threads > 0 ? cfg->threads : kClsThreads[c];
-        plan.cls_threads[c] = threads;
         int64_t n = plan.cls_end[c] - plan.cls_begin[c];
+        int threads = cfg->threads > 0 ? cfg->threads : kClsThreads[c];
+        if (cfg->threads == 0 && n > 0 && n < ctx->num_sms) {
+            // fewer items than SMs: every item has an SM to itself, so give it a block as wide as
+            // its widest level (each level step is then one task per thread)
+            int32_t wmax = 0;
+            for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) wmax = std::max(wmax, plan.items_h[(size_t)i].width);
+            int t = 128;
+            while (t < wmax && t < 1024) t *= 2;
+            threads = std::max(threads, t);
+        }
+        plan.cls_threads[c] = threads;
         if (n == 0) continue;
         int per_sm = 0;
         if (threads <= 256)

@@ -179,7 +179,7 @@ struct CfrItem {              // one work item of the CFR kernel: a root and a r
     int32_t root;
     int32_t tree;             // index into the launch's TreeView table
     int32_t ns;               // slots in the item
-    int32_t pad;
+    int32_t width;            // largest number of (active node, slot) pairs of one level
     int64_t s0;               // first slot of the item within its root
     int64_t data_base;        // offset of the item's (local node, slot) table in R and S
     int64_t scratch_base;     // offset in the global transients, or -1 when the item is resident
