@@ -63,6 +63,19 @@ __device__ __forceinline__ int at(int c, int a, int W, int w) {
     return W1 ? c + a : (c + a) * W + w;
 }
 
+// Pairwise sum of D values (a short dependency chain: about log2(D) additions deep).
+template <int D>
+__device__ __forceinline__ float tree_sum(const float *x) {
+    if (D == 1) return x[0];
+    if (D == 2) return x[0] + x[1];
+    constexpr int H = D / 2;
+    return tree_sum<H>(x) + tree_sum<D - H>(x + H);
+}
+
+// 1 / s for a positive regret sum: the fast reciprocal (at most 2 ulp; the sum is a normal
+// number, since counted regrets exceed the dead zone).
+__device__ __forceinline__ float rcp_pos(float s) { return __fdividef(1.f, s); }
+
 // Regret matching at one (active node, slot) with D children and the reach of the children.
 // X[n] holds the reach of the player who moved into node n; own = the mover's reach at the node.
 template <int D, bool W1>
@@ -72,21 +85,17 @@ __device__ __forceinline__ void td_node(int c, int W, int w, float own, const fl
         X[at<W1>(c, 0, W, w)] = own;
         return;
     }
-    float r[D];
+    float rp[D];
 #pragma unroll
-    for (int a = 0; a < D; a++) r[a] = R[at<W1>(c, a, W, w)];
-    float sum = 0.f;
-#pragma unroll
-    for (int a = 0; a < D; a++) sum += r[a] > thr ? r[a] : 0.f;
-    if (sum > 0.f) {
-        const float inv = 1.f / sum;
-#pragma unroll
-        for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = r[a] > thr ? own * (r[a] * inv) : 0.f;
-    } else {
-        const float u = own * (1.f / (float)D);
-#pragma unroll
-        for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = u;
+    for (int a = 0; a < D; a++) {
+        const float r = R[at<W1>(c, a, W, w)];
+        rp[a] = r > thr ? r : 0.f;
     }
+    const float sum = tree_sum<D>(rp);
+    const bool pos = sum > 0.f;
+    const float scale = pos ? own * rcp_pos(sum) : 0.f, u = own * (1.f / (float)D);
+#pragma unroll
+    for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = pos ? rp[a] * scale : u;
 }
 
 template <bool W1>
@@ -98,7 +107,7 @@ __device__ __forceinline__ void td_node_any(int c, int d, int W, int w, float ow
         sum += r > thr ? r : 0.f;
     }
     if (sum > 0.f) {
-        const float inv = 1.f / sum;
+        const float inv = rcp_pos(sum);
         for (int a = 0; a < d; a++) {
             const float r = R[at<W1>(c, a, W, w)];
             X[at<W1>(c, a, W, w)] = r > thr ? own * (r * inv) : 0.f;
@@ -115,30 +124,33 @@ template <int VARIANT, int D, bool W1>
 __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float spo, float *__restrict__ R,
                                          float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
                                          float fneg, float fs) {
-    float r[D], v[D];
+    float r[D], v[D], rp[D];
 #pragma unroll
     for (int a = 0; a < D; a++) {
         r[a] = R[at<W1>(c, a, W, w)];
         v[a] = V[at<W1>(c, a, W, w)];
+        rp[a] = r[a] > thr ? r[a] : 0.f;
     }
-    float sum = 0.f;
+    const float sum = tree_sum<D>(rp);
+    const bool pos = sum > 0.f;
+    const float inv = pos ? rcp_pos(sum) : 0.f, u = 1.f / (float)D;
+    float sg[D], dv[D];
 #pragma unroll
-    for (int a = 0; a < D; a++) sum += r[a] > thr ? r[a] : 0.f;
-    const float inv = sum > 0.f ? 1.f / sum : 0.f, u = 1.f / (float)D;
-    float vh = v[0];
-#pragma unroll
-    for (int a = 1; a < D; a++) vh += (sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u) * (v[a] - v[0]);
+    for (int a = 0; a < D; a++) {
+        sg[a] = pos ? rp[a] * inv : u;
+        dv[a] = a == 0 ? 0.f : sg[a] * (v[a] - v[0]);
+    }
+    const float vh = D == 1 ? v[0] : v[0] + tree_sum<D>(dv);
 #pragma unroll
     for (int a = 0; a < D; a++) {
         const int q = at<W1>(c, a, W, w);
-        const float sg = sum > 0.f ? (r[a] > thr ? r[a] * inv : 0.f) : u;
         const float inst = spo * (v[a] - vh);
         if (VARIANT == 1) {
             R[q] = r[a] * (r[a] > 0.f ? fpos : fneg) + inst;
-            S[q] = S[q] * fs + pp * sg;
+            S[q] = S[q] * fs + pp * sg[a];
         } else {
             R[q] = r[a] + inst;
-            S[q] = S[q] + pp * sg;
+            S[q] = S[q] + pp * sg[a];
         }
     }
     return vh;
@@ -153,7 +165,7 @@ __device__ __forceinline__ float bu_node_any(int c, int d, int W, int w, float p
         const float r = R[at<W1>(c, a, W, w)];
         sum += r > thr ? r : 0.f;
     }
-    const float inv = sum > 0.f ? 1.f / sum : 0.f, u = 1.f / (float)d;
+    const float inv = sum > 0.f ? rcp_pos(sum) : 0.f, u = 1.f / (float)d;
     const float v0 = V[at<W1>(c, 0, W, w)];
     float vh = v0;
     for (int a = 1; a < d; a++) {
