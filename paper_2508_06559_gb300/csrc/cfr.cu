@@ -870,13 +870,14 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         int64_t n = plan.cls_end[c] - plan.cls_begin[c];
         int threads = cfg->threads > 0 ? cfg->threads : kClsThreads[c];
         if (cfg->threads == 0 && n > 0 && n < ctx->num_sms) {
-            // fewer items than SMs: every item has an SM to itself, so give it a block as wide as
-            // its widest level (each level step is then one task per thread)
+            // fewer items than SMs: every item has an SM to itself, so widen its block towards its
+            // widest level (fewer tasks per thread per level step); beyond 256 threads the block
+            // barriers cost more than the shorter level steps save (measured on GB300)
             int32_t wmax = 0;
             for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) wmax = std::max(wmax, plan.items_h[(size_t)i].width);
             int t = 128;
-            while (t < wmax && t < 1024) t *= 2;
-            threads = std::max(threads, t);
+            while (t < wmax && t < 256) t *= 2;
+            threads = std::min(std::max(threads, t), std::max(t, 256));
         }
         plan.cls_threads[c] = threads;
         if (n == 0) continue;
