@@ -318,6 +318,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def recorded_traffic(workload: str, seed: int):
+    """DRAM bytes of the CFR kernel per step from the committed ncu record, when the workload is
+    the recorded one and the kernel source is unchanged since the capture; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_cfr_items_full_game_seed0.traffic.json")
+    if workload != "full_game" or seed != 0 or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["dram_bytes_read_per_solve"] + rec["dram_bytes_write_per_solve"]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -423,7 +440,8 @@ def run_ours(args, rank, world, dist):
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "cfr_kernel": {"ms_per_step": kernel_ms, "node_updates_per_s": updates / (kernel_ms / 1e3)},
         "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ach_gbs / hbm_peak,
-                     "traffic": None,
+                     "traffic": recorded_traffic(args.workload, args.seed),
+                     "traffic_unit": "bytes per step (all k_cfr_items launches of one solve; ncu record in profiles/)",
                      "note": (f"k_cfr_items; achieved = {ALG_BYTES_PER_UPDATE} B per node-update (R and S read + write) "
                               f"x node-updates / CFR kernel time, peak = {src} HBM copy bandwidth; the kernel keeps "
                               "each root's state in shared memory for all T iterations, so its DRAM traffic is far "
