@@ -330,6 +330,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_deal_seeds(workload: str, seed: int, rank: int):
+    """Seeds of the deals one rank solves: independent replicas, each rank its own deals (weak
+    scaling, no collective on the data path)."""
+    if workload == "batch64":
+        return [seed + rank * BATCH_DEALS + i for i in range(BATCH_DEALS)]
+    if workload == "surrogate16":
+        return [seed + rank * SUR_DEALS + i for i in range(SUR_DEALS)]
+    return [seed + rank]
+
+
+def reduce_over_ranks(dist, x: float, op: str, device) -> float:
+    """max or sum of a per-rank number over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(total_updates: float, slowest_seconds: float) -> float:
+    """Whole-job throughput: every rank's node-updates over the slowest rank's time."""
+    return total_updates / slowest_seconds
+
+
 def recorded_traffic(workload: str, seed: int):
     """DRAM bytes of the CFR kernel per step from the committed ncu record, when the workload is
     the recorded one and the kernel source is unchanged since the capture; else None."""
@@ -366,22 +391,20 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     ctx = P.Ctx(dev, 0, stream.cuda_stream)
     first_round, desc = WORKLOADS[args.workload]
-    seed = args.seed + rank
+    seeds = rank_deal_seeds(args.workload, args.seed, rank)
     T = args.iters
+    decks = np.stack([P.pasur_deal(s) for s in seeds])
+    for s, dk in zip(seeds, decks):
+        _DECK_SEEDS[bytes(dk)] = s
     if args.workload == "surrogate16":
-        base = args.seed + rank * SUR_DEALS
-        deck = np.stack([P.pasur_deal(base + i) for i in range(SUR_DEALS)])
+        deck = decks
         solve = solve_surrogate
         surrogate_setup(P, ctx, deck, T, torch)
     elif args.workload == "batch64":
-        base = args.seed + rank * BATCH_DEALS
-        deck = np.stack([P.pasur_deal(base + i) for i in range(BATCH_DEALS)])
-        for i in range(BATCH_DEALS):
-            _DECK_SEEDS[bytes(deck[i])] = base + i
+        deck = decks
         solve = solve_batch
     else:
-        deck = P.pasur_deal(seed)
-        _DECK_SEEDS[bytes(deck)] = seed
+        deck = decks[0]
         solve = solve_deal
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -409,11 +432,9 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
     launches = ctx.pasur_launch_count() - launches0
-    total_ms = sum(step_ms)
+    total_ms = reduce_over_ranks(dist, sum(step_ms), "max", "cuda")
+    job_updates = reduce_over_ranks(dist, float(updates), "sum", "cuda")
     if dist:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
 
     # end to end through the public API with host buffers (deck and pools in, results out)
@@ -427,18 +448,13 @@ def run_ours(args, rank, world, dist):
         _, _, d2h, h2d, _, _, _ = solve(P, ctx, deck, first_round, T, False, torch)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    if dist:
-        tt = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_mean = float(tt.item())
-    else:
-        e2e_mean = statistics.mean(e2e_ms)
+    e2e_mean = reduce_over_ranks(dist, statistics.mean(e2e_ms), "max", "cuda")
 
     if rank != 0:
         return None
     peaks, src = measured_peaks()
     ms_per_step = total_ms / args.steps
-    value = world * updates / (ms_per_step / 1e3)
+    value = job_rate(job_updates, ms_per_step / 1e3)
     kernel_ms = statistics.mean(kern_ms)
     # dominant kernel: the CFR kernel (k_cfr_items, one launch per size class and round); the
     # algorithmic traffic of CFR is the regret and strategy-sum read + write per node-update
@@ -459,7 +475,7 @@ def run_ours(args, rank, world, dist):
                               f"x node-updates / CFR kernel time, peak = {src} HBM copy bandwidth; the kernel keeps "
                               "each root's state in shared memory for all T iterations, so its DRAM traffic is far "
                               "below the algorithmic bytes (ncu counters in profiles/) and it is issue/latency bound")},
-        "e2e": {"value": world * updates / (e2e_mean / 1e3), "unit": "node-updates/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(job_updates, e2e_mean / 1e3), "unit": "node-updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(1, args.steps),
         "clocks": clk.summary(),
