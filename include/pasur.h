@@ -57,10 +57,15 @@ typedef struct {
  *                Umax = max |leaf value| in the subtree of the FGT root being solved (so each
  *                root's solve depends on its own subtree only), t = iteration index (1-based)
  *   dcfr_alpha/beta/gamma  DCFR discount exponents (the paper ran 1.5, 0, 2)
- *   slots_per_item  score slots solved together by one thread block (0 = choose automatically,
- *                at most 32)
+ *   slots_per_item  upper bound on the score slots solved together by one thread block (0 =
+ *                choose automatically, at most 32); every block takes a power-of-two number of
+ *                slots that fits its shared memory, results do not depend on the grouping
  *   threads      threads per block of the CFR kernel (0 = choose per subtree size, else a
  *                multiple of 32 up to 1024)
+ *   split_bytes  a root subtree whose state needs more shared memory than one block has is split
+ *                over a thread-block cluster (up to 16 SMs, distributed shared memory); with
+ *                split_bytes > 0 every subtree needing more than that many bytes is split too
+ *                (0 = only those that do not fit).  Results do not depend on the split.
  */
 typedef struct {
     int32_t variant;
@@ -69,6 +74,7 @@ typedef struct {
     float dcfr_alpha, dcfr_beta, dcfr_gamma;
     int32_t slots_per_item;
     int32_t threads;
+    int32_t split_bytes;
 } pasur_config;
 
 /* Fill *cfg with the defaults: vanilla, 1000 iterations, tau = 1e-6, DCFR (1.5, 0, 2). */

@@ -141,6 +141,7 @@ int pasur_config_default(pasur_config *cfg) {
     cfg->dcfr_gamma = 2.0f;
     cfg->slots_per_item = 0;
     cfg->threads = 0;
+    cfg->split_bytes = 0;
     return PASUR_OK;
 }
 
@@ -198,7 +199,7 @@ int pasur_destroy(pasur_ctx *ctx) {
     dev_free(ctx, ctx->counter, 64);
     dev_free(ctx, ctx->errflag, 64);
     cudaStreamSynchronize(ctx->stream);
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < 12; c++) {
         if (ctx->aux[c]) cudaStreamDestroy(ctx->aux[c]);
         if (ctx->join[c]) cudaEventDestroy(ctx->join[c]);
         if (ctx->cls_t0[c]) cudaEventDestroy(ctx->cls_t0[c]);

@@ -5,6 +5,8 @@
 // CFR, root utilities, round 5 down to the first round) is captured once into a CUDA graph and
 // replayed.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -124,6 +126,59 @@ int record_sweep(pasur_batch *b) {
     return PASUR_OK;
 }
 
+// Diagnostics (PASUR_VERBOSE): every round's merged plan per class, and the device time of each
+// round's CFR launches run once outside the graph on zeroed state (the batch is re-zeroed by
+// every pasur_batch_solve).
+int print_batch(pasur_batch *b) {
+    pasur_ctx *ctx = b->ctx;
+    for (int ri = b->n_rounds - 1; ri >= 0; ri--) {
+        CfrPlan &pl = b->plans[(size_t)ri];
+        for (int64_t d = 0; d < b->n_deals; d++) {
+            pasur_tree *t = tree_of(b, d, ri);
+            const float *next = ri + 1 < b->n_rounds ? b->util[(size_t)(d * b->n_rounds + ri + 1)]
+                                                     : (b->cut_util.empty() ? nullptr : b->cut_util[(size_t)d]);
+            PASUR_TRY(launch_leaf_values(t, next, nullptr));
+        }
+        cudaEvent_t e0, e1;
+        PASUR_CUDA(ctx, cudaEventCreate(&e0));
+        PASUR_CUDA(ctx, cudaEventCreate(&e1));
+        PASUR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        PASUR_TRY(cfr_launch_plan(ctx, pl, &b->cfg, 0, b->dcfr));
+        PASUR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        PASUR_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PASUR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        cfr_plan_times(ctx, pl);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (int64_t d = 0; d < b->n_deals; d++)
+            PASUR_TRY(cfr_export_utilities_n(tree_of(b, d, ri), b->cfg.iters, b->util[(size_t)(d * b->n_rounds + ri)]));
+        fprintf(stderr, "[pasur] batch round %d: %lld items, %d iterations in %.3f ms\n", b->first_round + ri,
+                (long long)pl.n_items, b->cfg.iters, ms);
+        for (int bk = 0; bk < 3; bk++)
+            if (pl.clu_end[bk] != pl.clu_begin[bk])
+                fprintf(stderr, "[pasur]   cluster items: %lld, %d CTAs x %d threads, smem %zu B, %.3f ms\n",
+                        (long long)(pl.clu_end[bk] - pl.clu_begin[bk]), pl.clu_ctas[bk], pl.clu_threads, pl.clu_smem[bk],
+                        pl.cls_ms[6 + bk]);
+        for (int c = 0; c < 8; c++) {
+            const int64_t n = pl.cls_end[c] - pl.cls_begin[c];
+            if (!n) continue;
+            int64_t cost = 0, slots = 0, maxcost = 0;
+            for (int64_t i = pl.cls_begin[c]; i < pl.cls_end[c]; i++) {
+                cost += pl.items_h[(size_t)i].cost;
+                slots += pl.items_h[(size_t)i].ns;
+                maxcost = std::max(maxcost, pl.items_h[(size_t)i].cost);
+            }
+            fprintf(stderr, "[pasur]   class %d: items %lld (slots %lld), smem %zu B, blocks %d x %d threads, "
+                            "active-node-slots %lld (largest item %lld), %.3f ms\n",
+                    c, (long long)n, (long long)slots, pl.cls_smem[c], pl.cls_blocks[c], pl.cls_threads[c], (long long)cost,
+                    (long long)maxcost, pl.cls_ms[c]);
+        }
+    }
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PASUR_OK;
+}
+
 }  // namespace
 }  // namespace pasur
 
@@ -204,10 +259,13 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
         std::vector<CfrItem> cls_items[8];
         size_t need[8] = {0};
         std::vector<TreeView> views;
+        std::vector<ClusterItem> clu;
+        size_t clu_smem = 0;
+        int clu_ctas = 0;
         for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
             pasur_tree *t = tree_of(b, d, ri);
             std::vector<CfrItem> own[8];
-            rc = cfr_setup_tree(t, cfg, (int)d, own, need);
+            rc = cfr_setup_tree(t, cfg, (int)d, own, need, &clu, &clu_smem, &clu_ctas);
             if (rc != PASUR_OK) break;
             t->cfr_ready = true;
             t->variant = cfg->variant;
@@ -228,7 +286,8 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
             views.push_back(t->view);
             b->edges += t->Q[1] + t->Q[2] + t->Q[3] + t->Q[4] + t->Q[5] + t->Q[6] + t->Q[7] + t->Q[8];
         }
-        if (rc == PASUR_OK) rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned);
+        if (rc == PASUR_OK)
+            rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu, clu_smem, clu_ctas);
     }
     if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
     if (rc == PASUR_OK && b->dcfr) b->owned.push_back({b->dcfr, b->dcfr_bytes});
@@ -245,6 +304,7 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
         rc = autotune(b, b->plans[(size_t)big]);
     }
     if (rc == PASUR_OK) rc = ensure_aux(ctx);
+    if (rc == PASUR_OK && getenv("PASUR_VERBOSE")) rc = print_batch(b);
     if (rc != PASUR_OK) {
         free_batch(b);
         delete b;

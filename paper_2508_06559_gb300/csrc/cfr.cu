@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 
 #include "pasur_internal.cuh"
 
@@ -31,7 +32,9 @@ namespace {
 constexpr int kNumCls = 6;
 constexpr size_t kClsBudget[kNumCls - 1] = {40 * 1024, 54 * 1024, 74 * 1024, 112 * 1024, 0 /* opt-in max */};
 constexpr int kClsGlobal = kNumCls - 1;
-constexpr int kClsThreads[kNumCls] = {128, 128, 256, 512, 1024, 256};
+constexpr int kClsCluster = 6;       // plan class of the cluster items' pseudo-items (exports only)
+constexpr int kMaxClusterCtas = 16;  // CTAs of a cluster (16: non-portable size)
+constexpr int kClsThreads[kNumCls] = {128, 128, 256, 512, 1024, 1024};
 
 struct CfrParams {
     const CfrItem *items;
@@ -53,14 +56,14 @@ __host__ __device__ __forceinline__ size_t resident_bytes(int64_t L, int64_t nA,
     return L >= 65535 ? ~(size_t)0 >> 1 : 2 * al16((size_t)nA * 4) + 4 * al16((size_t)L * W * 4);
 }
 
-constexpr int KC = 8;  // degrees with a fully unrolled path (larger degrees loop over memory)
 constexpr int kMaxSlots = 32;  // score slots per work item
 
-// Index of child edge a of a node whose first child is local node c, at slot w of an item of W
-// slots (slot-minor layout); W1: single-slot items, where this is c + a.
+// Index of child edge a of a node whose first child is local node c, at slot w of an item of
+// 2^sh slots (slot-minor layout; every item's slot count is a power of two); W1: single-slot
+// items, where this is c + a.
 template <bool W1>
-__device__ __forceinline__ int at(int c, int a, int W, int w) {
-    return W1 ? c + a : (c + a) * W + w;
+__device__ __forceinline__ int at(int c, int a, int sh, int w) {
+    return W1 ? c + a : ((c + a) << sh) + w;
 }
 
 // Pairwise sum of D values (a short dependency chain: about log2(D) additions deep).
@@ -79,56 +82,56 @@ __device__ __forceinline__ float rcp_pos(float s) { return __fdividef(1.f, s); }
 // Regret matching at one (active node, slot) with D children and the reach of the children.
 // X[n] holds the reach of the player who moved into node n; own = the mover's reach at the node.
 template <int D, bool W1>
-__device__ __forceinline__ void td_node(int c, int W, int w, float own, const float *__restrict__ R, float *__restrict__ X,
+__device__ __forceinline__ void td_node(int c, int sh, int w, float own, const float *__restrict__ R, float *__restrict__ X,
                                         float thr) {
-    if (D == 1) {
-        X[at<W1>(c, 0, W, w)] = own;
+    if constexpr (D == 1) {
+        X[at<W1>(c, 0, sh, w)] = own;
         return;
     }
     float rp[D];
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        const float r = R[at<W1>(c, a, W, w)];
+        const float r = R[at<W1>(c, a, sh, w)];
         rp[a] = r > thr ? r : 0.f;
     }
     const float sum = tree_sum<D>(rp);
     const bool pos = sum > 0.f;
     const float scale = pos ? own * rcp_pos(sum) : 0.f, u = own * (1.f / (float)D);
 #pragma unroll
-    for (int a = 0; a < D; a++) X[at<W1>(c, a, W, w)] = pos ? rp[a] * scale : u;
+    for (int a = 0; a < D; a++) X[at<W1>(c, a, sh, w)] = pos ? rp[a] * scale : u;
 }
 
 template <bool W1>
-__device__ __forceinline__ void td_node_any(int c, int d, int W, int w, float own, const float *__restrict__ R,
+__device__ __forceinline__ void td_node_any(int c, int d, int sh, int w, float own, const float *__restrict__ R,
                                             float *__restrict__ X, float thr) {
     float sum = 0.f;
     for (int a = 0; a < d; a++) {
-        const float r = R[at<W1>(c, a, W, w)];
+        const float r = R[at<W1>(c, a, sh, w)];
         sum += r > thr ? r : 0.f;
     }
     if (sum > 0.f) {
         const float inv = rcp_pos(sum);
         for (int a = 0; a < d; a++) {
-            const float r = R[at<W1>(c, a, W, w)];
-            X[at<W1>(c, a, W, w)] = r > thr ? own * (r * inv) : 0.f;
+            const float r = R[at<W1>(c, a, sh, w)];
+            X[at<W1>(c, a, sh, w)] = r > thr ? own * (r * inv) : 0.f;
         }
     } else {
         const float u = own * (1.f / (float)d);
-        for (int a = 0; a < d; a++) X[at<W1>(c, a, W, w)] = u;
+        for (int a = 0; a < d; a++) X[at<W1>(c, a, sh, w)] = u;
     }
 }
 
 // Value of one (active node, slot) with D children, then R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h))
 // and S(h,a) += pi_p(h) sigma(h,a) for its child edges.  Returns v(h).
 template <int VARIANT, int D, bool W1>
-__device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float spo, float *__restrict__ R,
+__device__ __forceinline__ float bu_node(int c, int sh, int w, float pp, float spo, float *__restrict__ R,
                                          float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
                                          float fneg, float fs) {
     float r[D], v[D], rp[D];
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        r[a] = R[at<W1>(c, a, W, w)];
-        v[a] = V[at<W1>(c, a, W, w)];
+        r[a] = R[at<W1>(c, a, sh, w)];
+        v[a] = V[at<W1>(c, a, sh, w)];
         rp[a] = r[a] > thr ? r[a] : 0.f;
     }
     const float sum = tree_sum<D>(rp);
@@ -143,7 +146,7 @@ __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float sp
     const float vh = D == 1 ? v[0] : v[0] + tree_sum<D>(dv);
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        const int q = at<W1>(c, a, W, w);
+        const int q = at<W1>(c, a, sh, w);
         const float inst = spo * (v[a] - vh);
         if (VARIANT == 1) {
             R[q] = r[a] * (r[a] > 0.f ? fpos : fneg) + inst;
@@ -157,23 +160,23 @@ __device__ __forceinline__ float bu_node(int c, int W, int w, float pp, float sp
 }
 
 template <int VARIANT, bool W1>
-__device__ __forceinline__ float bu_node_any(int c, int d, int W, int w, float pp, float spo, float *__restrict__ R,
+__device__ __forceinline__ float bu_node_any(int c, int d, int sh, int w, float pp, float spo, float *__restrict__ R,
                                              float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
                                              float fneg, float fs) {
     float sum = 0.f;
     for (int a = 0; a < d; a++) {
-        const float r = R[at<W1>(c, a, W, w)];
+        const float r = R[at<W1>(c, a, sh, w)];
         sum += r > thr ? r : 0.f;
     }
     const float inv = sum > 0.f ? rcp_pos(sum) : 0.f, u = 1.f / (float)d;
-    const float v0 = V[at<W1>(c, 0, W, w)];
+    const float v0 = V[at<W1>(c, 0, sh, w)];
     float vh = v0;
     for (int a = 1; a < d; a++) {
-        const float r = R[at<W1>(c, a, W, w)];
-        vh += (sum > 0.f ? (r > thr ? r * inv : 0.f) : u) * (V[at<W1>(c, a, W, w)] - v0);
+        const float r = R[at<W1>(c, a, sh, w)];
+        vh += (sum > 0.f ? (r > thr ? r * inv : 0.f) : u) * (V[at<W1>(c, a, sh, w)] - v0);
     }
     for (int a = 0; a < d; a++) {
-        const int q = at<W1>(c, a, W, w);
+        const int q = at<W1>(c, a, sh, w);
         const float r = R[q];
         const float sg = sum > 0.f ? (r > thr ? r * inv : 0.f) : u;
         const float inst = spo * (V[q] - vh);
@@ -222,99 +225,131 @@ struct Entries {
 // One level of the top-down pass over (active node, slot) pairs.  The active entries of a level
 // are sorted by degree, so the lanes of a warp mostly take the same unrolled path.
 template <int VARIANT, bool W1, bool PACKED>
-__device__ __forceinline__ void td_level(int b, int n, int W, int t0x, int stride, const Entries<PACKED> &A,
+__device__ __forceinline__ void td_level(int b, int n, int W, int sh, int t0x, int stride, const Entries<PACKED> &A,
                                          const float *__restrict__ R, float *__restrict__ X, const float *tu, float tf) {
     const float thr1 = tu[0] * tf;
     for (int x = t0x; x < n; x += stride) {
-        const int e = W1 ? b + x : b + x / W, w = W1 ? 0 : x % W;
+        const int e = W1 ? b + x : b + (x >> sh), w = W1 ? 0 : x & (W - 1);
         int c, d, li, pl;
         A.child(e, c, d);
         A.self(e, li, pl);
         const float thr = W1 ? thr1 : tu[w] * tf;
-        const float own = pl < 0 ? 1.f : X[W1 ? pl : pl * W + w];
+        const float own = pl < 0 ? 1.f : X[W1 ? pl : (pl << sh) + w];
         switch (d) {
-            case 1: td_node<1, W1>(c, W, w, own, R, X, thr); break;
-            case 2: td_node<2, W1>(c, W, w, own, R, X, thr); break;
-            case 3: td_node<3, W1>(c, W, w, own, R, X, thr); break;
-            case 4: td_node<4, W1>(c, W, w, own, R, X, thr); break;
-            case 5: td_node<5, W1>(c, W, w, own, R, X, thr); break;
-            case 6: td_node<6, W1>(c, W, w, own, R, X, thr); break;
-            case 7: td_node<7, W1>(c, W, w, own, R, X, thr); break;
-            case 8: td_node<8, W1>(c, W, w, own, R, X, thr); break;
-            default: td_node_any<W1>(c, d, W, w, own, R, X, thr);
+            case 1: td_node<1, W1>(c, sh, w, own, R, X, thr); break;
+            case 2: td_node<2, W1>(c, sh, w, own, R, X, thr); break;
+            case 3: td_node<3, W1>(c, sh, w, own, R, X, thr); break;
+            case 4: td_node<4, W1>(c, sh, w, own, R, X, thr); break;
+            case 5: td_node<5, W1>(c, sh, w, own, R, X, thr); break;
+            case 6: td_node<6, W1>(c, sh, w, own, R, X, thr); break;
+            case 7: td_node<7, W1>(c, sh, w, own, R, X, thr); break;
+            case 8: td_node<8, W1>(c, sh, w, own, R, X, thr); break;
+            default: td_node_any<W1>(c, d, sh, w, own, R, X, thr);
         }
     }
 }
 
 // One level of the bottom-up pass over (active node, slot) pairs.
 template <int VARIANT, bool W1, bool PACKED>
-__device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int t0x, int stride, const Entries<PACKED> &A,
+__device__ __forceinline__ void bu_level(bool alex, int b, int n, int W, int sh, int t0x, int stride,
+                                         const Entries<PACKED> &A,
                                          float *__restrict__ R, float *__restrict__ S, float *__restrict__ V,
                                          const float *__restrict__ X, const float *tu, float tf, float fpos, float fneg,
                                          float fs) {
     const float thr1 = tu[0] * tf;
     for (int x = t0x; x < n; x += stride) {
-        const int e = W1 ? b + x : b + x / W, w = W1 ? 0 : x % W;
+        const int e = W1 ? b + x : b + (x >> sh), w = W1 ? 0 : x & (W - 1);
         int c, d, li, pl;
         A.child(e, c, d);
         A.self(e, li, pl);
         const float thr = W1 ? thr1 : tu[w] * tf;
-        const float pp = pl < 0 ? 1.f : X[W1 ? pl : pl * W + w];  // pi_p(h)
-        const float po = X[W1 ? li : li * W + w];                 // pi_{-p}(h)
+        const float pp = pl < 0 ? 1.f : X[W1 ? pl : (pl << sh) + w];  // pi_p(h)
+        const float po = X[W1 ? li : (li << sh) + w];                 // pi_{-p}(h)
         const float spo = alex ? po : -po;
         float vh;
         switch (d) {
-            case 1: vh = bu_node<VARIANT, 1, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 2: vh = bu_node<VARIANT, 2, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 3: vh = bu_node<VARIANT, 3, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 4: vh = bu_node<VARIANT, 4, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 5: vh = bu_node<VARIANT, 5, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 6: vh = bu_node<VARIANT, 6, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 7: vh = bu_node<VARIANT, 7, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            case 8: vh = bu_node<VARIANT, 8, W1>(c, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-            default: vh = bu_node_any<VARIANT, W1>(c, d, W, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
+            case 1: vh = bu_node<VARIANT, 1, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 2: vh = bu_node<VARIANT, 2, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 3: vh = bu_node<VARIANT, 3, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 4: vh = bu_node<VARIANT, 4, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 5: vh = bu_node<VARIANT, 5, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 6: vh = bu_node<VARIANT, 6, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 7: vh = bu_node<VARIANT, 7, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 8: vh = bu_node<VARIANT, 8, W1>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            default: vh = bu_node_any<VARIANT, W1>(c, d, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
         }
-        V[W1 ? li : li * W + w] = vh;
+        V[W1 ? li : (li << sh) + w] = vh;
     }
 }
 
-// The T iterations of one item over its level schedule: sched[i] for i < 7 the top-down levels
-// 0..6, for i >= 7 the bottom-up levels 7..0; each (first entry, pairs, flags: 1 = empty, 2 = at
-// most 32 pairs (warp 0 alone), 4 = the next non-empty level is also small (a warp barrier
-// suffices)).
+// Level steps i0..i1-1 of a level schedule: sched[i] for i < 7 the top-down levels 0..6, for
+// i >= 7 the bottom-up levels 7..0; each (first entry, pairs, flags: 1 = empty, 2 = at most 32
+// pairs (warp 0 alone), 4 = the next non-empty level of the same pass is also small (a warp
+// barrier suffices)).
+template <int VARIANT, bool W1, bool PACKED>
+__device__ __forceinline__ void run_passes(int i0, int i1, int W, int sh, const Entries<PACKED> &A, float *R, float *S,
+                                           float *V, float *X, const int32_t *sb, const int32_t *sn, const int32_t *sf,
+                                           const float *s_tu, float tf, float fpos, float fneg, float fs) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const bool warp0 = tid < 32;
+    for (int i = i0; i < i1; i++) {
+        const int f = sf[i];
+        if (f & 1) continue;
+        if (i < 7) {
+            if (!(f & 2)) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, sh, tid, nth, A, R, X, s_tu, tf);
+            else if (warp0) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, sh, tid, 32, A, R, X, s_tu, tf);
+        } else {
+            const bool alex = ((14 - i) & 1) == 0;
+            if (!(f & 2)) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, sh, tid, nth, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+            else if (warp0) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, sh, tid, 32, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
+        }
+        if (f & 4) __syncwarp();
+        else __syncthreads();
+    }
+}
+
+// The level schedule of an entry layout with level starts as[0..9] and W slots (thread 0).
+__device__ __forceinline__ void make_schedule(const int32_t *as, int W, int32_t *sb, int32_t *sn, int32_t *sf) {
+    for (int i = 0; i < 15; i++) {
+        const int k = i < 7 ? i : 14 - i;
+        sb[i] = as[k];
+        sn[i] = (as[k + 1] - as[k]) * W;
+    }
+    for (int i = 0; i < 15; i++) {
+        int f = sn[i] == 0 ? 1 : 0;
+        const bool small = sn[i] <= 32;
+        if (small) f |= 2;
+        const int end = i < 7 ? 7 : 15;
+        int j = i + 1;
+        while (j < end && sn[j] == 0) j++;
+        if (small && j < end && sn[j] <= 32) f |= 4;
+        sf[i] = f;
+    }
+}
+
+template <int VARIANT>
+__device__ __forceinline__ void dcfr_factors(const CfrParams &p, int il, float &fpos, float &fneg, float &fs) {
+    fpos = fneg = fs = 0.f;
+    if (VARIANT == 1) {
+        fpos = p.dcfr[3 * il];
+        fneg = p.dcfr[3 * il + 1];
+        fs = p.dcfr[3 * il + 2];
+    }
+}
+
+// The T iterations of one item over its level schedule.
 template <int VARIANT, bool W1, bool PACKED>
 __device__ __forceinline__ double iterate(const CfrParams &p, int W, const Entries<PACKED> &A, float *R, float *S,
                                           float *V, float *X, const int32_t *sb, const int32_t *sn, const int32_t *sf,
                                           const float *s_tu) {
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const bool warp0 = tid < 32;
+    const int tid = threadIdx.x;
+    const int sh = __ffs(W) - 1;  // W is a power of two
     double acc = 0.0;
     for (int il = 0; il < p.iters; il++) {
-        const int64_t t = p.t0 + il + 1;
-        const float tf = (float)t;
-        float fpos = 0.f, fneg = 0.f, fs = 0.f;
-        if (VARIANT == 1) {
-            fpos = p.dcfr[3 * il];
-            fneg = p.dcfr[3 * il + 1];
-            fs = p.dcfr[3 * il + 2];
-        }
-        for (int i = 0; i < 7; i++) {
-            const int f = sf[i];
-            if (f & 1) continue;
-            if (!(f & 2)) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, tid, nth, A, R, X, s_tu, tf);
-            else if (warp0) td_level<VARIANT, W1, PACKED>(sb[i], sn[i], W, tid, 32, A, R, X, s_tu, tf);
-            if (f & 4) __syncwarp();
-            else __syncthreads();
-        }
-        for (int i = 7; i < 15; i++) {
-            const int f = sf[i];
-            if (f & 1) continue;
-            const bool alex = ((14 - i) & 1) == 0;
-            if (!(f & 2)) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, tid, nth, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
-            else if (warp0) bu_level<VARIANT, W1, PACKED>(alex, sb[i], sn[i], W, tid, 32, A, R, S, V, X, s_tu, tf, fpos, fneg, fs);
-            if (f & 4) __syncwarp();
-            else __syncthreads();
-        }
+        const float tf = (float)(p.t0 + il + 1);
+        float fpos, fneg, fs;
+        dcfr_factors<VARIANT>(p, il, fpos, fneg, fs);
+        run_passes<VARIANT, W1, PACKED>(0, 15, W, sh, A, R, S, V, X, sb, sn, sf, s_tu, tf, fpos, fneg, fs);
         if (tid < W) acc += (double)V[tid];
         __syncthreads();
     }
@@ -383,24 +418,7 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv,
     }
     // level schedule: a level of at most 32 (node, slot) pairs runs on warp 0 alone, and only a
     // change between warp-0 and whole-block levels needs a block barrier
-    if (tid == 0) {
-        for (int i = 0; i < 15; i++) {
-            const int k = i < 7 ? i : 14 - i;
-            sb[i] = s_as[k];
-            sn[i] = (s_as[k + 1] - s_as[k]) * W;
-        }
-        for (int i = 0; i < 15; i++) {
-            int f = sn[i] == 0 ? 1 : 0;
-            const bool small = sn[i] <= 32;
-            if (small) f |= 2;
-            // next non-empty level in execution order within the same pass
-            const int end = i < 7 ? 7 : 15;
-            int j = i + 1;
-            while (j < end && sn[j] == 0) j++;
-            if (small && j < end && sn[j] <= 32) f |= 4;
-            sf[i] = f;
-        }
-    }
+    if (tid == 0) make_schedule(s_as, W, sb, sn, sf);
     __syncthreads();
     for (int w = tid; w < W; w += nth) s_tu[w] = p.tau * s_tu[w];
     __syncthreads();
@@ -443,6 +461,213 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrPara
         if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
         else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
     }
+}
+
+// ---- a root subtree split over a thread-block cluster ------------------------------------------
+//
+// CTA r of the cluster holds part r (subtrees of active level-ell nodes) in its shared memory;
+// CTA 0 also holds the top levels 0..ell-1.  Per iteration: CTA 0 runs the top-down pass of the
+// top and pushes, for every active level-ell node, its reach and its parent's reach into the
+// owning CTA's shared memory (distributed shared memory); cluster barrier; every CTA runs both
+// passes over its part and pushes the node values back to CTA 0; cluster barrier; CTA 0 runs the
+// bottom-up pass of the top.  Every task does the same arithmetic as in a single block.
+
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+// all threads of all CTAs of the cluster; shared::cluster writes before it are visible after it
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of the same shared-memory byte in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ float cl_ld(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// byte offsets of a resident single-slot region (entries cd, lp, then R, S, V, X)
+struct RegionOffsets {
+    uint32_t lp, R, S, V, X, end;
+};
+__host__ __device__ __forceinline__ RegionOffsets region_offsets(int64_t L, int64_t nA) {
+    RegionOffsets o;
+    o.lp = (uint32_t)al16((size_t)nA * 4);
+    o.R = o.lp + (uint32_t)al16((size_t)nA * 4);
+    o.S = o.R + (uint32_t)al16((size_t)L * 4);
+    o.V = o.S + (uint32_t)al16((size_t)L * 4);
+    o.X = o.V + (uint32_t)al16((size_t)L * 4);
+    o.end = o.X + (uint32_t)al16((size_t)L * 4);
+    return o;
+}
+
+// load a single-slot region (packed entries, R, S; terminal values into V) and return the largest
+// |terminal value|
+__device__ __forceinline__ float load_region(const TreeView &tv, const CfrRoot &cr, int64_t data_base, int64_t slot,
+                                             unsigned char *base, Entries<true> &E, float *&R, float *&S, float *&V,
+                                             float *&X) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int L = cr.ls[9], nA = cr.as[9];
+    const RegionOffsets o = region_offsets(L, nA);
+    uint32_t *cd = (uint32_t *)base, *lp = (uint32_t *)(base + o.lp);
+    R = (float *)(base + o.R);
+    S = (float *)(base + o.S);
+    V = (float *)(base + o.V);
+    X = (float *)(base + o.X);
+    const int32_t *gli = tv.act_li + cr.act_off, *gpl = tv.act_pl + cr.act_off, *gcs = tv.act_cs + cr.act_off;
+    const uint16_t *gd = tv.act_d + cr.act_off;
+    for (int i = tid; i < nA; i += nth) {
+        cd[i] = (uint32_t)gcs[i] | ((uint32_t)gd[i] << 16);
+        lp[i] = (uint32_t)gli[i] | ((uint32_t)(gpl[i] < 0 ? 0xFFFF : gpl[i]) << 16);
+    }
+    const float *gR = tv.R + data_base, *gS = tv.S + data_base;
+    const int64_t *tq = tv.loc_tq + cr.loc_off;
+    float umax = 0.f;
+    for (int i = tid; i < L; i += nth) {
+        R[i] = gR[i];
+        S[i] = gS[i];
+        const int64_t q = tq[i];
+        if (q >= 0) {
+            const float v = tv.leaf_v[q + slot];
+            V[i] = v;
+            umax = fmaxf(umax, fabsf(v));
+        }
+    }
+    E.cd = cd;
+    E.lp = lp;
+    return umax;
+}
+
+__device__ __forceinline__ void store_region(const TreeView &tv, const CfrRoot &cr, int64_t data_base, const float *R,
+                                             const float *S) {
+    const int L = cr.ls[9];
+    float *gR = tv.R + data_base, *gS = tv.S + data_base;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        gR[i] = R[i];
+        gS[i] = S[i];
+    }
+}
+
+template <int VARIANT>
+__global__ void __launch_bounds__(1024, 1) k_cfr_cluster(CfrParams p, const ClusterItem *__restrict__ clu) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int32_t s_as[10], t_as[10];
+    __shared__ int32_t s_sb[15], s_sn[15], s_sf[15], t_sb[15], t_sn[15], t_sf[15];
+    __shared__ float s_tu[1];
+    __shared__ unsigned s_umax;
+    __shared__ float s_qmax[kMaxClusterCtas];
+    __shared__ uint32_t s_xoff[kMaxClusterCtas];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t q = cl_rank(), nq = cl_count();
+    const ClusterItem c = clu[cl_id()];
+    const TreeView tv = p.views[c.tree];
+    const bool has_part = (int)q < c.nparts;
+    const ClusterPart top = tv.cparts[c.part0];
+    const ClusterPart part0 = tv.cparts[c.part0 + 1];
+    const CfrRoot &tr = tv.roots[top.root];
+    const CfrRoot &pr0 = tv.roots[part0.root];
+    // CTA 0: part 0 at offset 0, the top right after it
+    const uint32_t top_base = region_offsets(pr0.ls[9], pr0.as[9]).end;
+    const uint32_t top_v = top_base + region_offsets(tr.ls[9], tr.as[9]).V;
+    Entries<true> PE{}, TE{};
+    float *PR = nullptr, *PS = nullptr, *PV = nullptr, *PX = nullptr;
+    float *TR = nullptr, *TS = nullptr, *TV = nullptr, *TX = nullptr;
+    if (tid == 0) s_umax = 0u;
+    if (tid < (int)nq && q == 0) {
+        const int r = tid;
+        if (r < c.nparts) {
+            const CfrRoot &prr = tv.roots[tv.cparts[c.part0 + 1 + r].root];
+            s_xoff[r] = region_offsets(prr.ls[9], prr.as[9]).X;
+        } else {
+            s_xoff[r] = 0;
+        }
+    }
+    __syncthreads();
+    float um = 0.f;
+    const ClusterPart mine = has_part ? tv.cparts[c.part0 + 1 + q] : part0;
+    const CfrRoot &pr = tv.roots[mine.root];
+    if (has_part) um = load_region(tv, pr, mine.data_base, c.s0, sm, PE, PR, PS, PV, PX);
+    if (q == 0) um = fmaxf(um, load_region(tv, tr, top.data_base, c.s0, sm + top_base, TE, TR, TS, TV, TX));
+    atomicMax(&s_umax, __float_as_uint(um));
+    if (tid < 10) {
+        s_as[tid] = has_part ? pr.as[tid] : 0;
+        t_as[tid] = tr.as[tid];
+    }
+    __syncthreads();
+    if (q == 0 && tid == 0) TX[0] = 1.f;  // root reach
+    if (tid == 0) {
+        make_schedule(s_as, 1, s_sb, s_sn, s_sf);
+        make_schedule(t_as, 1, t_sb, t_sn, t_sf);
+        cl_st(cl_map(&s_qmax[q], 0), __uint_as_float(s_umax));
+    }
+    cl_sync();
+    if (tid == 0) {
+        float m = 0.f;
+        for (uint32_t r = 0; r < nq; r++) m = fmaxf(m, cl_ld(cl_map(&s_qmax[r], 0)));
+        s_tu[0] = p.tau * m;
+    }
+    __syncthreads();
+    const int32_t *cx = tv.cx + 5 * c.x0;
+    double acc = 0.0;
+    for (int il = 0; il < p.iters; il++) {
+        const float tf = (float)(p.t0 + il + 1);
+        float fpos, fneg, fs;
+        dcfr_factors<VARIANT>(p, il, fpos, fneg, fs);
+        if (q == 0) {
+            run_passes<VARIANT, true, true>(0, 7, 1, 0, TE, TR, TS, TV, TX, t_sb, t_sn, t_sf, s_tu, tf, fpos, fneg, fs);
+            // reaches of the active level-ell nodes and of their parents, into their owners
+            for (int j = tid; j < c.nx; j += nth) {
+                const int32_t *e = cx + 5 * j;
+                const uint32_t r = (uint32_t)e[0];
+                unsigned char *xb = sm + s_xoff[r];
+                cl_st(cl_map(xb + 4 * e[3], r), TX[e[1]]);
+                cl_st(cl_map(xb + 4 * e[4], r), TX[e[2]]);
+            }
+        }
+        cl_sync();
+        if (has_part) {
+            run_passes<VARIANT, true, true>(0, 15, 1, 0, PE, PR, PS, PV, PX, s_sb, s_sn, s_sf, s_tu, tf, fpos, fneg, fs);
+            // values of my active level-ell nodes, into the top
+            for (int j = tid; j < c.nx; j += nth) {
+                const int32_t *e = cx + 5 * j;
+                if ((uint32_t)e[0] == q) cl_st(cl_map(sm + top_v + 4 * e[1], 0), PV[e[3]]);
+            }
+        }
+        cl_sync();
+        if (q == 0) {
+            run_passes<VARIANT, true, true>(7, 15, 1, 0, TE, TR, TS, TV, TX, t_sb, t_sn, t_sf, s_tu, tf, fpos, fneg, fs);
+            if (tid == 0) acc += (double)TV[0];
+        }
+    }
+    if (has_part) store_region(tv, pr, mine.data_base, PR, PS);
+    if (q == 0) {
+        store_region(tv, tr, top.data_base, TR, TS);
+        if (tid == 0) {
+            if (!isfinite(acc)) atomicOr(p.err, 1);
+            tv.uacc[tv.fgt_off0[c.root] + c.s0] += acc;
+        }
+    }
+    cl_sync();  // no CTA leaves while another may still address its shared memory
 }
 
 struct LevelPtrs {
@@ -724,6 +949,223 @@ int build_layout(pasur_tree *t) {
 
 }  // namespace
 
+// ---- roots split over thread-block clusters ----------------------------------------------------
+
+
+struct SplitRoot {
+    int32_t ell = 0, nparts = 0;
+    int32_t top_root = 0, part_root0 = 0;   // pseudo-root ids
+    int64_t x0 = 0;
+    int32_t nx = 0;
+    int64_t top_L = 0;
+    std::vector<int64_t> part_L;            // local nodes incl. ghosts
+    size_t smem = 0;                         // largest CTA need (CTA 0: part 0 + top)
+};
+
+namespace {
+
+// Plan the split of every root that needs a cluster: subtrees of the active level-ell nodes packed
+// (in GT order) into parts that each fit one block; CTA 0 also holds the top levels.  Appends the
+// pseudo-roots to croots_h, their entries and local-node leaf indices to the host vectors, and
+// the exchange entries to t->cx_h.
+int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t part_max, std::vector<SplitRoot> &splits,
+                std::vector<int32_t> &split_of, std::vector<int32_t> &nli, std::vector<int32_t> &npl,
+                std::vector<int32_t> &ncs, std::vector<uint16_t> &nd, std::vector<int64_t> &ngt,
+                std::vector<int64_t> &ntq) {
+    pasur_ctx *ctx = t->ctx;
+    const int64_t nr = t->n_roots;
+    split_of.assign((size_t)nr, -1);
+    std::vector<int64_t> cand;
+    for (int64_t g = 0; g < nr; g++) {
+        const CfrRoot &cr = t->croots_h[(size_t)g];
+        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t L = cr.ls[9], nA = cr.as[9];
+        if (Sg == 0 || L == 0 || nA < 2) continue;
+        const size_t need = resident_bytes(L, nA, 1);
+        if (need > dyn_max || (cfg->split_bytes > 0 && need > (size_t)cfg->split_bytes)) cand.push_back(g);
+    }
+    if (cand.empty()) return PASUR_OK;
+    // host copies of the layout
+    const int64_t NA = t->n_active, NL = t->n_local;
+    std::vector<int32_t> hli((size_t)NA), hpl((size_t)NA), hcs((size_t)NA);
+    std::vector<uint16_t> hd((size_t)NA);
+    std::vector<int64_t> hgt((size_t)NA), htq((size_t)NL);
+    PASUR_CUDA(ctx, cudaMemcpy(hli.data(), t->act_li, sizeof(int32_t) * (size_t)NA, cudaMemcpyDeviceToHost));
+    PASUR_CUDA(ctx, cudaMemcpy(hpl.data(), t->act_pl, sizeof(int32_t) * (size_t)NA, cudaMemcpyDeviceToHost));
+    PASUR_CUDA(ctx, cudaMemcpy(hcs.data(), t->act_cs, sizeof(int32_t) * (size_t)NA, cudaMemcpyDeviceToHost));
+    PASUR_CUDA(ctx, cudaMemcpy(hd.data(), t->act_d, sizeof(uint16_t) * (size_t)NA, cudaMemcpyDeviceToHost));
+    PASUR_CUDA(ctx, cudaMemcpy(hgt.data(), t->act_gt, sizeof(int64_t) * (size_t)NA, cudaMemcpyDeviceToHost));
+    PASUR_CUDA(ctx, cudaMemcpy(htq.data(), t->loc_tq, sizeof(int64_t) * (size_t)NL, cudaMemcpyDeviceToHost));
+    const size_t target = cfg->split_bytes > 0 ? std::min<size_t>((size_t)cfg->split_bytes, part_max) : part_max;
+    for (int64_t g : cand) {
+        const CfrRoot cr = t->croots_h[(size_t)g];
+        const int64_t L = cr.ls[9], nA = cr.as[9];
+        const int32_t *li = hli.data() + cr.act_off, *pl = hpl.data() + cr.act_off, *cs = hcs.data() + cr.act_off;
+        const uint16_t *dd = hd.data() + cr.act_off;
+        bool done = false;
+        for (int ell = 1; ell <= 6 && !done; ell++) {
+            const int32_t e0 = cr.as[ell], e1 = cr.as[ell + 1];
+            if (e1 - e0 < 2) continue;
+            // subtree id of every local node at levels >= ell below an active level-ell node
+            std::vector<int32_t> heads;  // local indices of the active level-ell nodes, GT order
+            for (int32_t e = e0; e < e1; e++) heads.push_back(li[e]);
+            std::sort(heads.begin(), heads.end());
+            std::vector<int32_t> sub((size_t)L, -1), ent_of((size_t)L, -1);
+            for (int32_t e = 0; e < nA; e++) ent_of[(size_t)li[e]] = e;
+            for (size_t i = 0; i < heads.size(); i++) sub[(size_t)heads[i]] = (int32_t)i;
+            const int ns = (int)heads.size();
+            std::vector<int64_t> sa((size_t)ns, 0), sl((size_t)ns, 0);
+            for (int k = ell; k < 8; k++)
+                for (int32_t e = cr.as[k]; e < cr.as[k + 1]; e++) {
+                    const int32_t sid = sub[(size_t)li[e]];
+                    if (sid < 0) continue;
+                    sa[(size_t)sid]++;
+                    for (int a = 0; a < dd[e]; a++) sub[(size_t)(cs[e] + a)] = sid;
+                }
+            for (int64_t x = cr.ls[ell]; x < L; x++)
+                if (sub[(size_t)x] >= 0) sl[(size_t)sub[(size_t)x]]++;
+            const size_t top_bytes = resident_bytes(cr.ls[ell + 1], cr.as[ell], 1);
+            if (top_bytes >= part_max) break;
+            // pack the subtrees into parts (contiguous runs), balancing active entries
+            int64_t tot = 0;
+            for (int i = 0; i < ns; i++) tot += sa[(size_t)i];
+            // parts: the target size sets the starting count (portable clusters of up to 8 CTAs
+            // first), a block's shared memory is the hard limit of every part
+            const size_t need = resident_bytes(L, nA, 1);
+            const int q0 = (int)std::min<size_t>(cfg->split_bytes > 0 ? kMaxClusterCtas : 8,
+                                                 std::max<size_t>(2, (need + target - 1) / target));
+            // contiguous parts: greedy fill with an entry cap (and the byte limit); the smallest
+            // cap that needs at most Q parts, by bisection
+            auto greedy = [&](int64_t cap, std::vector<int> &first) -> bool {
+                first.assign(1, 0);
+                int64_t pa = 0, plc = 0, pg = 0;
+                for (int i = 0; i < ns; i++) {
+                    const size_t lim = first.size() == 1 ? part_max - top_bytes : part_max;
+                    const bool fits = resident_bytes(plc + sl[(size_t)i] + pg + 1, pa + sa[(size_t)i], 1) <= lim;
+                    if (pa > 0 && (!fits || pa + sa[(size_t)i] > cap)) {
+                        first.push_back(i);
+                        pa = plc = pg = 0;
+                    }
+                    const size_t lim2 = first.size() == 1 ? part_max - top_bytes : part_max;
+                    pa += sa[(size_t)i];
+                    plc += sl[(size_t)i];
+                    pg += 1;
+                    if (resident_bytes(plc + pg, pa, 1) > lim2) return false;
+                }
+                return true;
+            };
+            int64_t amax = 0;
+            for (int i = 0; i < ns; i++) amax = std::max(amax, sa[(size_t)i]);
+            for (int Q = q0; Q <= kMaxClusterCtas && !done; Q++) {
+                std::vector<int> first;
+                int64_t lo = std::max<int64_t>(amax, (tot + Q - 1) / Q), hi = tot;
+                if (!greedy(hi, first) || (int)first.size() > Q) {
+                    // even unlimited entries per part need more than Q parts (byte limit)
+                    if (!greedy(hi, first)) break;  // a single subtree does not fit a block
+                    continue;
+                }
+                while (lo < hi) {
+                    const int64_t mid = lo + (hi - lo) / 2;
+                    if (greedy(mid, first) && (int)first.size() <= Q) hi = mid;
+                    else lo = mid + 1;
+                }
+                if (!greedy(lo, first) || (int)first.size() > Q) continue;
+                first.push_back(ns);
+                const int np = (int)first.size() - 1;
+                // build the parts
+                SplitRoot sr;
+                sr.ell = ell;
+                sr.nparts = np;
+                sr.top_root = (int32_t)t->croots_h.size();
+                sr.part_root0 = sr.top_root + 1;
+                sr.x0 = (int64_t)t->cx_h.size() / 5;
+                sr.top_L = cr.ls[ell + 1];
+                CfrRoot top = cr;
+                for (int k = ell + 1; k < 10; k++) top.as[k] = cr.as[ell];
+                for (int k = ell + 2; k < 10; k++) top.ls[k] = cr.ls[ell + 1];
+                top.W = 1;
+                top.cls = kClsCluster;
+                t->croots_h.push_back(top);
+                std::vector<int32_t> part_of_sub((size_t)ns);
+                for (int q = 0; q < np; q++)
+                    for (int i = first[(size_t)q]; i < first[(size_t)q + 1]; i++) part_of_sub[(size_t)i] = q;
+                std::vector<int32_t> newidx((size_t)L, -1), ghost((size_t)L, -1);
+                size_t smax = 0;
+                for (int q = 0; q < np; q++) {
+                    CfrRoot pr{};
+                    int64_t n = 0;
+                    for (int k = 0; k <= ell; k++) pr.ls[k] = 0;
+                    for (int k = ell; k <= 8; k++) {
+                        pr.ls[k] = (int32_t)n;
+                        for (int64_t x = cr.ls[k]; x < cr.ls[k + 1]; x++) {
+                            const int32_t sid = sub[(size_t)x];
+                            if (sid >= 0 && part_of_sub[(size_t)sid] == q) newidx[(size_t)x] = (int32_t)n++;
+                        }
+                    }
+                    for (int i = first[(size_t)q]; i < first[(size_t)q + 1]; i++) ghost[(size_t)heads[(size_t)i]] = (int32_t)n++;
+                    pr.ls[9] = (int32_t)n;
+                    pr.loc_off = (int64_t)(NL + ntq.size());
+                    pr.act_off = (int64_t)(NA + nli.size());
+                    std::vector<int64_t> tq((size_t)n, -1);
+                    for (int64_t x = cr.ls[ell]; x < L; x++) {
+                        const int32_t sid = sub[(size_t)x];
+                        if (sid >= 0 && part_of_sub[(size_t)sid] == q) tq[(size_t)newidx[(size_t)x]] = htq[(size_t)(cr.loc_off + x)];
+                    }
+                    ntq.insert(ntq.end(), tq.begin(), tq.end());
+                    int32_t m = 0;
+                    for (int k = 0; k <= ell; k++) pr.as[k] = 0;
+                    for (int k = ell; k < 8; k++) {
+                        pr.as[k] = m;
+                        for (int32_t e = cr.as[k]; e < cr.as[k + 1]; e++) {
+                            const int32_t sid = sub[(size_t)li[e]];
+                            if (sid < 0 || part_of_sub[(size_t)sid] != q) continue;
+                            nli.push_back(newidx[(size_t)li[e]]);
+                            npl.push_back(k == ell ? ghost[(size_t)li[e]] : newidx[(size_t)pl[e]]);
+                            ncs.push_back(newidx[(size_t)cs[e]]);
+                            nd.push_back(dd[e]);
+                            ngt.push_back(hgt[(size_t)(cr.act_off + e)]);
+                            m++;
+                        }
+                    }
+                    pr.as[8] = pr.as[9] = m;
+                    pr.W = 1;
+                    pr.cls = kClsCluster;
+                    t->croots_h.push_back(pr);
+                    sr.part_L.push_back(n);
+                    size_t b = resident_bytes(n, m, 1);
+                    if (q == 0) b += resident_bytes(sr.top_L, cr.as[ell], 1);
+                    smax = std::max(smax, b);
+                }
+                // exchange entries: active level-ell nodes
+                for (size_t i = 0; i < heads.size(); i++) {
+                    const int32_t x = heads[i];
+                    const int32_t e = ent_of[(size_t)x];
+                    t->cx_h.push_back(part_of_sub[i]);
+                    t->cx_h.push_back(x);
+                    t->cx_h.push_back(pl[e]);
+                    t->cx_h.push_back(newidx[(size_t)x]);
+                    t->cx_h.push_back(ghost[(size_t)x]);
+                }
+                sr.nx = (int32_t)heads.size();
+                sr.smem = smax;
+                split_of[(size_t)g] = (int32_t)splits.size();
+                splits.push_back(sr);
+                done = true;
+            }
+            if (!done && getenv("PASUR_VERBOSE")) {
+                int64_t big = 0;
+                for (int i = 0; i < ns; i++) big = std::max<int64_t>(big, (int64_t)resident_bytes(sl[(size_t)i] + 1, sa[(size_t)i], 1));
+                fprintf(stderr, "[pasur] root %lld (L %lld, active %lld): no split at level %d: %d subtrees, top %zu B, "
+                                "largest subtree %lld B, part limit %zu B\n",
+                        (long long)g, (long long)L, (long long)nA, ell, ns, top_bytes, (long long)big, part_max);
+            }
+        }
+    }
+    return PASUR_OK;
+}
+
+}  // namespace
+
 // Largest dynamic shared memory a CFR block may request: the per-block opt-in limit minus the
 // kernel's own static shared memory (largest over its instantiations).
 int cfr_dyn_smem_limit(pasur_ctx *ctx, size_t *limit) {
@@ -741,7 +1183,10 @@ int cfr_dyn_smem_limit(pasur_ctx *ctx, size_t *limit) {
     return PASUR_OK;
 }
 
-int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need) {
+int cfr_cluster_smem_limit(pasur_ctx *ctx, size_t *limit);
+
+int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need,
+                   std::vector<ClusterItem> *clu, size_t *clu_smem, int *clu_ctas) {
     pasur_ctx *ctx = t->ctx;
     PASUR_TRY(build_layout(t));
     // every root goes to the smallest shared-memory class its subtree fits with one slot; its
@@ -751,6 +1196,17 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     size_t budget[kNumCls - 1];
     for (int c = 0; c < kNumCls - 1; c++) budget[c] = kClsBudget[c] ? std::min<size_t>(kClsBudget[c], dyn_max) : dyn_max;
     const int wcap = cfg->slots_per_item > 0 ? std::min(cfg->slots_per_item, kMaxSlots) : kMaxSlots;
+    // roots too large for one block (or above cfg->split_bytes) go to thread-block clusters
+    std::vector<SplitRoot> splits;
+    std::vector<int32_t> split_of, nli, npl, ncs;
+    std::vector<uint16_t> nd;
+    std::vector<int64_t> ngt, ntq;
+    t->croots_h.resize((size_t)t->n_roots);
+    t->cparts_h.clear();
+    t->cx_h.clear();
+    size_t dyn_cl = 0;
+    PASUR_TRY(cfr_cluster_smem_limit(ctx, &dyn_cl));
+    PASUR_TRY(plan_splits(t, cfg, dyn_max, std::min(dyn_max, dyn_cl), splits, split_of, nli, npl, ncs, nd, ngt, ntq));
     int64_t data = 0, scratch = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         CfrRoot &cr = t->croots_h[(size_t)g];
@@ -759,22 +1215,60 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
         cr.W = 0;
         cr.cls = -1;
         if (Sg == 0 || L == 0) continue;
+        if (split_of[(size_t)g] >= 0) {
+            const SplitRoot sr = splits[(size_t)split_of[(size_t)g]];
+            cr.W = 1;
+            cr.cls = kClsCluster;
+            for (int64_t s0 = 0; s0 < Sg; s0++) {
+                ClusterItem ci{};
+                ci.tree = tree;
+                ci.root = (int32_t)g;
+                ci.s0 = s0;
+                ci.part0 = (int64_t)t->cparts_h.size();
+                ci.x0 = sr.x0;
+                ci.nx = sr.nx;
+                ci.nparts = sr.nparts;
+                ci.ell = sr.ell;
+                ci.smem = (int32_t)sr.smem;
+                for (int q = -1; q < sr.nparts; q++) {
+                    const int32_t r = q < 0 ? sr.top_root : sr.part_root0 + q;
+                    const int64_t n = q < 0 ? sr.top_L : sr.part_L[(size_t)q];
+                    t->cparts_h.push_back(ClusterPart{r, 0, data});
+                    CfrItem it{};
+                    it.root = r;
+                    it.tree = tree;
+                    it.ns = 1;
+                    it.s0 = s0;
+                    it.data_base = data;
+                    it.scratch_base = -1;
+                    it.cost = std::max<int64_t>(t->croots_h[(size_t)r].as[9], 1);
+                    cls_items[kClsCluster].push_back(it);
+                    data += n;
+                }
+                clu->push_back(ci);
+            }
+            *clu_smem = std::max(*clu_smem, sr.smem);
+            *clu_ctas = std::max(*clu_ctas, sr.nparts);
+            continue;
+        }
         int cls = kClsGlobal;
         for (int c = 0; c < kNumCls - 1; c++)
             if (resident_bytes(L, nA, 1) <= budget[c]) {
                 cls = c;
                 break;
             }
-        int64_t w = std::min<int64_t>(Sg, wcap);
-        if (cls != kClsGlobal)
-            while (w > 1 && resident_bytes(L, nA, w) > budget[cls]) w--;
+        // slots per item: a power of two (the kernel indexes slots with shifts), the largest that
+        // fits the class; the remaining slots of the root go to power-of-two items too
+        int64_t w = 1;
+        while (w * 2 <= std::min<int64_t>(Sg, wcap) && (cls == kClsGlobal || resident_bytes(L, nA, w * 2) <= budget[cls])) w *= 2;
         cr.W = (int32_t)w;
         cr.cls = cls;
-        for (int64_t s0 = 0; s0 < Sg; s0 += w) {
+        for (int64_t s0 = 0, ns = w; s0 < Sg; s0 += ns) {
+            while (ns > Sg - s0) ns /= 2;
             CfrItem it{};
             it.root = (int32_t)g;
             it.tree = tree;
-            it.ns = (int32_t)std::min<int64_t>(w, Sg - s0);
+            it.ns = (int32_t)ns;
             it.s0 = s0;
             it.data_base = data;
             data += L * it.ns;
@@ -794,8 +1288,46 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     }
     t->data_size = data;
     t->scratch_size = scratch;
-    if (t->n_roots > 0)
-        PASUR_CUDA(ctx, cudaMemcpyAsync(t->croots_d, t->croots_h.data(), sizeof(CfrRoot) * (size_t)t->n_roots,
+    if (!splits.empty()) {
+        // append the parts' entries and local leaf indices; pseudo-roots after the real roots
+        const int64_t NA = t->n_active, NL = t->n_local, na = (int64_t)nli.size(), nl = (int64_t)ntq.size();
+        int32_t *li = nullptr, *pl = nullptr, *cs = nullptr;
+        uint16_t *d = nullptr;
+        int64_t *gt = nullptr, *tq = nullptr;
+        PASUR_TRY(tree_alloc(t, (void **)&li, sizeof(int32_t) * (size_t)(NA + na + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&pl, sizeof(int32_t) * (size_t)(NA + na + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&cs, sizeof(int32_t) * (size_t)(NA + na + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&d, sizeof(uint16_t) * (size_t)(NA + na + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&gt, sizeof(int64_t) * (size_t)(NA + na + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&tq, sizeof(int64_t) * (size_t)(NL + nl + 1)));
+        auto cp = [&](void *dst, const void *old_d, size_t ob, const void *new_h, size_t nb) -> int {
+            PASUR_CUDA(ctx, cudaMemcpyAsync(dst, old_d, ob, cudaMemcpyDeviceToDevice, ctx->stream));
+            PASUR_CUDA(ctx, cudaMemcpyAsync((char *)dst + ob, new_h, nb, cudaMemcpyHostToDevice, ctx->stream));
+            return PASUR_OK;
+        };
+        PASUR_TRY(cp(li, t->act_li, 4 * (size_t)NA, nli.data(), 4 * (size_t)na));
+        PASUR_TRY(cp(pl, t->act_pl, 4 * (size_t)NA, npl.data(), 4 * (size_t)na));
+        PASUR_TRY(cp(cs, t->act_cs, 4 * (size_t)NA, ncs.data(), 4 * (size_t)na));
+        PASUR_TRY(cp(d, t->act_d, 2 * (size_t)NA, nd.data(), 2 * (size_t)na));
+        PASUR_TRY(cp(gt, t->act_gt, 8 * (size_t)NA, ngt.data(), 8 * (size_t)na));
+        PASUR_TRY(cp(tq, t->loc_tq, 8 * (size_t)NL, ntq.data(), 8 * (size_t)nl));
+        t->act_li = li;
+        t->act_pl = pl;
+        t->act_cs = cs;
+        t->act_d = d;
+        t->act_gt = gt;
+        t->loc_tq = tq;
+        PASUR_TRY(tree_alloc(t, (void **)&t->croots_d, sizeof(CfrRoot) * t->croots_h.size()));
+        PASUR_TRY(tree_alloc(t, (void **)&t->cparts_d, sizeof(ClusterPart) * (t->cparts_h.size() + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&t->cx_d, sizeof(int32_t) * (t->cx_h.size() + 1)));
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->cparts_d, t->cparts_h.data(), sizeof(ClusterPart) * t->cparts_h.size(),
+                                        cudaMemcpyHostToDevice, ctx->stream));
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->cx_d, t->cx_h.data(), sizeof(int32_t) * t->cx_h.size(), cudaMemcpyHostToDevice,
+                                        ctx->stream));
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    if (!t->croots_h.empty())
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->croots_d, t->croots_h.data(), sizeof(CfrRoot) * t->croots_h.size(),
                                         cudaMemcpyHostToDevice, ctx->stream));
     PASUR_TRY(tree_alloc(t, (void **)&t->R, sizeof(float) * (size_t)(data + 1)));
     PASUR_TRY(tree_alloc(t, (void **)&t->S, sizeof(float) * (size_t)(data + 1)));
@@ -821,25 +1353,63 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     v.V = t->V;
     v.X = t->X;
     v.uacc = t->uacc;
+    v.cparts = t->cparts_d;
+    v.cx = t->cx_d;
     t->iters_done = 0;
     t->cfr_ready = true;
     return PASUR_OK;
 }
 
+int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg);
+
 int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
-                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned) {
+                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned,
+                      const std::vector<ClusterItem> &clu, size_t clu_smem, int clu_ctas) {
     if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
         return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
+    if (cfg->split_bytes < 0) return set_err(ctx, PASUR_EINVAL, "cfg.split_bytes must be >= 0");
     plan.items_h.clear();
-    for (int c = 0; c < kNumCls; c++) {
+    // classes 0..5 are launched by k_cfr_items; class 6 holds the cluster items' pseudo-items
+    for (int c = 0; c <= kClsCluster; c++) {
         std::stable_sort(cls_items[c].begin(), cls_items[c].end(),
                          [](const CfrItem &a, const CfrItem &b) { return a.cost > b.cost; });
         plan.cls_begin[c] = (int64_t)plan.items_h.size();
         plan.items_h.insert(plan.items_h.end(), cls_items[c].begin(), cls_items[c].end());
         plan.cls_end[c] = (int64_t)plan.items_h.size();
-        plan.cls_smem[c] = need[c];
+        plan.cls_smem[c] = c < kNumCls ? need[c] : 0;
     }
     plan.n_items = (int64_t)plan.items_h.size();
+    (void)clu_smem;
+    (void)clu_ctas;
+    plan.clu_h = clu;
+    std::stable_sort(plan.clu_h.begin(), plan.clu_h.end(),
+                     [](const ClusterItem &a, const ClusterItem &b) { return a.nparts < b.nparts; });
+    for (int b = 0; b < 3; b++) {
+        plan.clu_begin[b] = plan.clu_end[b] = 0;
+        plan.clu_smem[b] = 0;
+    }
+    int64_t i = 0;
+    for (int b = 0; b < 3; b++) {
+        plan.clu_begin[b] = i;
+        while (i < (int64_t)plan.clu_h.size() && plan.clu_h[(size_t)i].nparts <= plan.clu_ctas[b]) {
+            plan.clu_smem[b] = std::max(plan.clu_smem[b], (size_t)plan.clu_h[(size_t)i].smem);
+            i++;
+        }
+        plan.clu_end[b] = i;
+    }
+    // one block width for the cluster launches: 1024 threads when a part fills an SM's shared
+    // memory, narrower when several parts can share an SM
+    size_t cmax = 0;
+    for (int b = 0; b < 3; b++) cmax = std::max(cmax, plan.clu_smem[b]);
+    plan.clu_threads = cmax <= 72 * 1024 ? 256 : (cmax <= 112 * 1024 ? 512 : 1024);
+    if (cfg->threads > 0) plan.clu_threads = cfg->threads;
+    if (!plan.clu_h.empty()) {
+        size_t b = sizeof(ClusterItem) * plan.clu_h.size();
+        PASUR_TRY(dev_alloc(ctx, (void **)&plan.clu_d, b));
+        owned.push_back({plan.clu_d, b});
+        PASUR_CUDA(ctx, cudaMemcpyAsync(plan.clu_d, plan.clu_h.data(), b, cudaMemcpyHostToDevice, ctx->stream));
+        PASUR_TRY(cfr_cluster_check(ctx, &plan, cfg));
+    }
     if (plan.n_items) {
         size_t b = sizeof(CfrItem) * (size_t)plan.n_items;
         PASUR_TRY(dev_alloc(ctx, (void **)&plan.items_d, b));
@@ -878,6 +1448,9 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
             int t = 128;
             while (t < wmax && t < 256) t *= 2;
             threads = std::min(std::max(threads, t), std::max(t, 256));
+            // items whose state lives in device memory wait on L2/DRAM latency at every access:
+            // they take a whole SM each, so give them the widest block for latency hiding
+            if (c == kClsGlobal) threads = 1024;
         }
         plan.cls_threads[c] = threads;
         if (n == 0) continue;
@@ -923,7 +1496,7 @@ int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float 
 int ensure_aux(pasur_ctx *ctx) {
     if (ctx->fork) return PASUR_OK;
     PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
-    for (int c = 0; c < kNumCls; c++) {
+    for (int c = 0; c < kClsCluster + 3; c++) {
         PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
         PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
         PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
@@ -970,6 +1543,80 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
         PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
         PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
     }
+    // roots split over thread-block clusters: one cluster per item, a launch (and a stream) per
+    // cluster size
+    for (int b = 0; b < 3; b++) {
+        const int64_t n = plan.clu_end[b] - plan.clu_begin[b];
+        if (n == 0) continue;
+        const int c = kClsCluster + b;
+        cudaStream_t st = ctx->aux[c];
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3((unsigned)(n * plan.clu_ctas[b]), 1, 1);
+        lc.blockDim = dim3((unsigned)plan.clu_threads, 1, 1);
+        lc.dynamicSmemBytes = plan.clu_smem[b];
+        lc.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)plan.clu_ctas[b];
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        const ClusterItem *ci = plan.clu_d + plan.clu_begin[b];
+        if (cfg->variant == 1) PASUR_CUDA(ctx, cudaLaunchKernelEx(&lc, k_cfr_cluster<1>, p, ci));
+        else PASUR_CUDA(ctx, cudaLaunchKernelEx(&lc, k_cfr_cluster<0>, p, ci));
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
+    }
+    return PASUR_OK;
+}
+
+// Prepare the cluster kernel for a plan's cluster items: shared-memory and cluster-size
+// attributes, and a check that one cluster of this shape can be resident.
+int cfr_cluster_smem_limit(pasur_ctx *ctx, size_t *limit) {
+    size_t st = 0;
+    cudaFuncAttributes fa;
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_cluster<0>));
+    st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_cluster<1>));
+    st = std::max(st, fa.sharedSizeBytes);
+    *limit = ctx->smem_optin > st ? ctx->smem_optin - st : 0;
+    return PASUR_OK;
+}
+
+int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg) {
+    (void)cfg;
+    size_t lim = 0;
+    PASUR_TRY(cfr_cluster_smem_limit(ctx, &lim));
+    const void *ks[2] = {(const void *)k_cfr_cluster<0>, (const void *)k_cfr_cluster<1>};
+    for (const void *k : ks) {
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
+    for (int b = 0; b < 3; b++) {
+        if (plan->clu_end[b] == plan->clu_begin[b]) continue;
+        if (plan->clu_smem[b] > lim) return set_err(ctx, PASUR_EINVAL, "cluster part exceeds the shared memory of a block");
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3((unsigned)plan->clu_ctas[b], 1, 1);
+        lc.blockDim = dim3((unsigned)plan->clu_threads, 1, 1);
+        lc.dynamicSmemBytes = plan->clu_smem[b];
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)plan->clu_ctas[b];
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        int nclusters = 0;
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_cfr_cluster<0>, &lc));
+        if (nclusters < 1)
+            return set_err(ctx, PASUR_EINVAL, "a cluster of " + std::to_string(plan->clu_ctas[b]) + " blocks of " +
+                                                  std::to_string(plan->clu_smem[b]) + " B shared memory cannot be resident");
+    }
     return PASUR_OK;
 }
 
@@ -978,6 +1625,11 @@ void cfr_plan_times(pasur_ctx *ctx, CfrPlan &plan) {
         float m = 0.f;
         if (plan.cls_end[c] != plan.cls_begin[c]) cudaEventElapsedTime(&m, ctx->cls_t0[c], ctx->cls_t1[c]);
         plan.cls_ms[c] = m;
+    }
+    for (int b = 0; b < 3; b++) {
+        float m = 0.f;
+        if (plan.clu_end[b] != plan.clu_begin[b]) cudaEventElapsedTime(&m, ctx->cls_t0[kClsCluster + b], ctx->cls_t1[kClsCluster + b]);
+        plan.cls_ms[kClsCluster + b] = m;
     }
 }
 
@@ -994,15 +1646,22 @@ static void print_plan(const pasur_tree *t, const CfrPlan &plan) {
         fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld\n", c,
                 (long long)n, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost);
     }
+    for (int b = 0; b < 3; b++)
+        if (plan.clu_end[b] != plan.clu_begin[b])
+            fprintf(stderr, "[pasur]   cluster items: %lld, %d CTAs x %d threads, smem %zu B\n",
+                    (long long)(plan.clu_end[b] - plan.clu_begin[b]), plan.clu_ctas[b], plan.clu_threads, plan.clu_smem[b]);
 }
 
 int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
     pasur_ctx *ctx = t->ctx;
-    std::vector<CfrItem> cls_items[kNumCls];
-    size_t need[kNumCls] = {0};
-    PASUR_TRY(cfr_setup_tree(t, cfg, 0, cls_items, need));
+    std::vector<CfrItem> cls_items[8];
+    size_t need[8] = {0};
+    std::vector<ClusterItem> clu;
+    size_t clu_smem = 0;
+    int clu_ctas = 0;
+    PASUR_TRY(cfr_setup_tree(t, cfg, 0, cls_items, need, &clu, &clu_smem, &clu_ctas));
     std::vector<std::pair<void *, size_t>> owned;
-    int rc = cfr_finalize_plan(ctx, t->plan, cls_items, need, {t->view}, cfg, owned);
+    int rc = cfr_finalize_plan(ctx, t->plan, cls_items, need, {t->view}, cfg, owned, clu, clu_smem, clu_ctas);
     for (auto &o : owned) {
         t->allocs.push_back(o.first);
         t->allocs.push_back((void *)(uintptr_t)o.second);

@@ -129,8 +129,10 @@ struct pasur_ctx {
     int32_t *counter = nullptr;  // work-queue counters (device)
     int32_t *errflag = nullptr;  // device error word
     int64_t launches = 0;        // kernels launched through this context
-    cudaStream_t aux[8] = {nullptr};  // forked streams for concurrent launches (created on first use)
-    cudaEvent_t fork = nullptr, join[8] = {nullptr}, cls_t0[8] = {nullptr}, cls_t1[8] = {nullptr};
+    // forked streams for concurrent launches (created on first use): CFR classes 0..5, cluster
+    // launches 6..8
+    cudaStream_t aux[12] = {nullptr};
+    cudaEvent_t fork = nullptr, join[12] = {nullptr}, cls_t0[12] = {nullptr}, cls_t1[12] = {nullptr};
     int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
     bool cfr_smem_raised = false;  // CFR kernels' dynamic shared-memory limit raised
     float selfplay_ms = 0.f;     // device time of the last self-play launch
@@ -163,6 +165,26 @@ struct CfrRoot {
     int64_t item0;            // index of its first work item
 };
 
+// A root subtree too large for one block's shared memory, split over a thread-block cluster:
+// CTA 0 holds the top levels 0..ell-1 (and part 0), CTA r holds part r, a set of subtrees of
+// active level-ell nodes.  Parts and top are pseudo-roots (CfrRoot records appended after the real
+// roots) with their own local numbering; each active level-ell node has a ghost slot in its part
+// for its parent's reach.
+struct ClusterPart {
+    int32_t root;             // pseudo-root
+    int32_t pad;
+    int64_t data_base;        // its regrets and strategy sums in R and S
+};
+
+struct ClusterItem {
+    int32_t tree, root;       // launch tree index, real GT root
+    int64_t s0;               // slot (one per cluster item)
+    int64_t part0;            // cparts[part0] = top, cparts[part0 + 1 + r] = part r
+    int64_t x0;               // exchange entries cx[x0 .. x0 + nx) (5 ints each)
+    int32_t nx, nparts;
+    int32_t ell, smem;        // split level; shared memory of its largest CTA
+};
+
 // Per-tree pointers of the CFR kernel (one entry per round tree of a launch).
 struct TreeView {
     const CfrRoot *roots;
@@ -173,6 +195,8 @@ struct TreeView {
     const int64_t *fgt_off0;
     float *R, *S, *V, *X;
     double *uacc;
+    const ClusterPart *cparts;   // cluster items: parts table
+    const int32_t *cx;           // cluster items: (part, top node, top parent, part node, part ghost)
 };
 
 struct CfrItem {              // one work item of the CFR kernel: a root and a run of its slots
@@ -196,7 +220,15 @@ struct CfrPlan {
     size_t cls_smem[8] = {0};
     int cls_blocks[8] = {0};
     int cls_threads[8] = {0};
-    float cls_ms[8] = {0};
+    float cls_ms[12] = {0};
+    // cluster items (class 6 holds their pseudo-items, used for exports only), sorted by part
+    // count into up to three launches of 4, 8 and 16 CTAs per cluster
+    std::vector<ClusterItem> clu_h;
+    ClusterItem *clu_d = nullptr;
+    int clu_threads = 0;
+    int64_t clu_begin[3] = {0}, clu_end[3] = {0};
+    int clu_ctas[3] = {4, 8, 16};
+    size_t clu_smem[3] = {0};
 };
 
 struct pasur_tree {
@@ -244,6 +276,10 @@ struct pasur_tree {
     int64_t *act_gt = nullptr;          //   GT node index
     int64_t *loc_tq = nullptr;          // per local node: FGT index (slot 0) of its chain's leaf, -1 if active
     int64_t n_local = 0, n_active = 0;
+    std::vector<ClusterPart> cparts_h;  // cluster items of this tree
+    std::vector<int32_t> cx_h;
+    ClusterPart *cparts_d = nullptr;
+    int32_t *cx_d = nullptr;
     CfrPlan plan;                       // this tree alone
     TreeView view{};                    // its pointers for the CFR kernel
     int64_t data_size = 0, scratch_size = 0;
@@ -302,10 +338,14 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg);
 int cfr_run(pasur_tree *t, const pasur_config *cfg);
 // layout, per-root plan and state of one tree; its items (tagged with tree index `tree`) are
 // appended per class to cls_items, the shared-memory need per class raised in need[]
-int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need);
+// (cls_items / need: 8 classes; roots split over clusters append ClusterItems to clu and raise
+// clu_smem / clu_ctas)
+int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need,
+                   std::vector<ClusterItem> *clu, size_t *clu_smem, int *clu_ctas);
 // sort and upload merged items and the tree views; launch configuration per class
 int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
-                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned);
+                      const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned,
+                      const std::vector<ClusterItem> &clu, size_t clu_smem, int clu_ctas);
 // launch the plan's classes for cfg->iters iterations starting at iteration t0 (+1); no host
 // synchronisation (capturable); per-class times are read by cfr_plan_times
 int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int64_t t0, const float *dcfr);
