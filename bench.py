@@ -221,32 +221,50 @@ def surrogate_setup(P, ctx, decks, T, torch):
     torch.cuda.synchronize()
     exact_s = time.perf_counter() - t1
     _, exact_edges, _ = be.pasur_batch_stats()
-    res = {"exact": [], "surrogate": [], "no_learning": [], "mse_surrogate": [], "mse_no_learning": []}
-    cuts = {}
-    for key, net in (("surrogate", mlp), ("no_learning", none)):
-        bs = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
-        bs.pasur_batch_solve()
-        cuts[key] = bs
-    for d in range(len(decks)):
-        te = [be.pasur_batch_tree(d, r) for r in range(6)]
-        res["exact"].append((P.chain_values(te, 1)[0] - P.chain_values(te, 2)[0]) / 2)
-        u3 = te[3].pasur_round_utilities()
+    # the surrogate at two cut points: after round 3 (rounds 1-3 solved; the timed form) and after
+    # round 4 (rounds 1-4 solved, the network values round-5 roots)
+    expl_exact = []
+    res = {}
+    cut_s = {}
+    for last in (2, 3):
         for key, net in (("surrogate", mlp), ("no_learning", none)):
-            ts = [cuts[key].pasur_batch_tree(d, r) for r in range(3)]
-            sig = [t.pasur_avg_strategy() for t in ts] + [None] * 3
-            res[key].append((P.chain_values(te, 1, sig)[0] - P.chain_values(te, 2, sig)[0]) / 2)
-            res["mse_" + key].append(float(((net.predict_next(ts[2]) - u3) ** 2).mean()))
-    for bs in cuts.values():
-        bs.free()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            bs = P.Batch(ctx, decks, 0, cfg, last_round=last, mlp=net)
+            bs.pasur_batch_solve()
+            torch.cuda.synchronize()
+            cut_s[(key, last)] = time.perf_counter() - t2
+            ex, mse = [], []
+            for d in range(len(decks)):
+                te = [be.pasur_batch_tree(d, r) for r in range(6)]
+                if last == 2 and key == "surrogate":
+                    expl_exact.append((P.chain_values(te, 1)[0] - P.chain_values(te, 2)[0]) / 2)
+                ts = [bs.pasur_batch_tree(d, r) for r in range(last + 1)]
+                sig = [t.pasur_avg_strategy() for t in ts] + [None] * (5 - last)
+                ex.append((P.chain_values(te, 1, sig)[0] - P.chain_values(te, 2, sig)[0]) / 2)
+                u_next = te[last + 1].pasur_round_utilities()
+                mse.append(float(((net.predict_next(ts[last]) - u_next) ** 2).mean()))
+            res[(key, last)] = (ex, mse)
+            bs.free()
     be.free()
     none.free()
+    cuts = {}
+    for last in (2, 3):
+        cuts[f"rounds 1-{last + 1} solved, network at round-{last + 2} roots"] = {
+            "create_solve_s": {k: cut_s[(k, last)] for k in ("surrogate", "no_learning")},
+            "speedup_vs_exact": exact_s / cut_s[("surrogate", last)],
+            "exploitability_mean": {k: float(np.mean(res[(k, last)][0])) for k in ("surrogate", "no_learning")},
+            "exploitability_per_deal": {k: [round(float(x), 4) for x in res[(k, last)][0]] for k in ("surrogate", "no_learning")},
+            "root_value_mse": {k: float(np.mean(res[(k, last)][1])) for k in ("surrogate", "no_learning")}}
     _SUR.update(mlp=mlp, info={
         "train_deals": SUR_TRAIN_DEALS, "train_rows": mlp.dataset_size(), "label_iters": SUR_LABEL_ITERS,
         "data_gen_s": gen_s, "train_ms": train_ms, "adam_steps": steps, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
         "exact_batch_s": exact_s, "exact_node_updates": exact_edges * T,
-        "exploitability_mean": {k: float(np.mean(res[k])) for k in ("exact", "surrogate", "no_learning")},
-        "exploitability_per_deal": {k: [round(float(x), 4) for x in res[k]] for k in ("exact", "surrogate", "no_learning")},
-        "round4_root_mse": {"surrogate": float(np.mean(res["mse_surrogate"])), "no_learning": float(np.mean(res["mse_no_learning"]))},
+        "exploitability_mean": {"exact": float(np.mean(expl_exact)),
+                                "surrogate": float(np.mean(res[("surrogate", 2)][0])),
+                                "no_learning": float(np.mean(res[("no_learning", 2)][0]))},
+        "exploitability_per_deal_exact": [round(float(x), 4) for x in expl_exact],
+        "cuts": cuts,
         "target_gap": 1e-3})
 
 
