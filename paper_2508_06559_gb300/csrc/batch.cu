@@ -260,12 +260,10 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
         size_t need[8] = {0};
         std::vector<TreeView> views;
         std::vector<ClusterItem> clu;
-        size_t clu_smem = 0;
-        int clu_ctas = 0;
         for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
             pasur_tree *t = tree_of(b, d, ri);
             std::vector<CfrItem> own[8];
-            rc = cfr_setup_tree(t, cfg, (int)d, own, need, &clu, &clu_smem, &clu_ctas);
+            rc = cfr_setup_tree(t, cfg, (int)d, own, need, &clu);
             if (rc != PASUR_OK) break;
             t->cfr_ready = true;
             t->variant = cfg->variant;
@@ -287,7 +285,7 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
             b->edges += t->Q[1] + t->Q[2] + t->Q[3] + t->Q[4] + t->Q[5] + t->Q[6] + t->Q[7] + t->Q[8];
         }
         if (rc == PASUR_OK)
-            rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu, clu_smem, clu_ctas);
+            rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu);
     }
     if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
     if (rc == PASUR_OK && b->dcfr) b->owned.push_back({b->dcfr, b->dcfr_bytes});

@@ -1186,7 +1186,7 @@ int cfr_dyn_smem_limit(pasur_ctx *ctx, size_t *limit) {
 int cfr_cluster_smem_limit(pasur_ctx *ctx, size_t *limit);
 
 int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need,
-                   std::vector<ClusterItem> *clu, size_t *clu_smem, int *clu_ctas) {
+                   std::vector<ClusterItem> *clu) {
     pasur_ctx *ctx = t->ctx;
     PASUR_TRY(build_layout(t));
     // every root goes to the smallest shared-memory class its subtree fits with one slot; its
@@ -1247,8 +1247,6 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
                 }
                 clu->push_back(ci);
             }
-            *clu_smem = std::max(*clu_smem, sr.smem);
-            *clu_ctas = std::max(*clu_ctas, sr.nparts);
             continue;
         }
         int cls = kClsGlobal;
@@ -1364,7 +1362,7 @@ int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg);
 
 int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
                       const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned,
-                      const std::vector<ClusterItem> &clu, size_t clu_smem, int clu_ctas) {
+                      const std::vector<ClusterItem> &clu) {
     if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
         return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
     if (cfg->split_bytes < 0) return set_err(ctx, PASUR_EINVAL, "cfg.split_bytes must be >= 0");
@@ -1379,8 +1377,6 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         plan.cls_smem[c] = c < kNumCls ? need[c] : 0;
     }
     plan.n_items = (int64_t)plan.items_h.size();
-    (void)clu_smem;
-    (void)clu_ctas;
     plan.clu_h = clu;
     std::stable_sort(plan.clu_h.begin(), plan.clu_h.end(),
                      [](const ClusterItem &a, const ClusterItem &b) { return a.nparts < b.nparts; });
@@ -1657,11 +1653,9 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
     std::vector<CfrItem> cls_items[8];
     size_t need[8] = {0};
     std::vector<ClusterItem> clu;
-    size_t clu_smem = 0;
-    int clu_ctas = 0;
-    PASUR_TRY(cfr_setup_tree(t, cfg, 0, cls_items, need, &clu, &clu_smem, &clu_ctas));
+    PASUR_TRY(cfr_setup_tree(t, cfg, 0, cls_items, need, &clu));
     std::vector<std::pair<void *, size_t>> owned;
-    int rc = cfr_finalize_plan(ctx, t->plan, cls_items, need, {t->view}, cfg, owned, clu, clu_smem, clu_ctas);
+    int rc = cfr_finalize_plan(ctx, t->plan, cls_items, need, {t->view}, cfg, owned, clu);
     for (auto &o : owned) {
         t->allocs.push_back(o.first);
         t->allocs.push_back((void *)(uintptr_t)o.second);

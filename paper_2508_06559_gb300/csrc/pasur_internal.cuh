@@ -338,14 +338,13 @@ int cfr_prepare(pasur_tree *t, const pasur_config *cfg);
 int cfr_run(pasur_tree *t, const pasur_config *cfg);
 // layout, per-root plan and state of one tree; its items (tagged with tree index `tree`) are
 // appended per class to cls_items, the shared-memory need per class raised in need[]
-// (cls_items / need: 8 classes; roots split over clusters append ClusterItems to clu and raise
-// clu_smem / clu_ctas)
+// (cls_items / need: 8 classes; roots split over thread-block clusters append ClusterItems to clu)
 int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need,
-                   std::vector<ClusterItem> *clu, size_t *clu_smem, int *clu_ctas);
+                   std::vector<ClusterItem> *clu);
 // sort and upload merged items and the tree views; launch configuration per class
 int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_items, const size_t *need,
                       const std::vector<TreeView> &views, const pasur_config *cfg, std::vector<std::pair<void *, size_t>> &owned,
-                      const std::vector<ClusterItem> &clu, size_t clu_smem, int clu_ctas);
+                      const std::vector<ClusterItem> &clu);
 // launch the plan's classes for cfg->iters iterations starting at iteration t0 (+1); no host
 // synchronisation (capturable); per-class times are read by cfr_plan_times
 int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int64_t t0, const float *dcfr);
