@@ -25,16 +25,23 @@ int cuda_err(pasur_ctx *ctx, cudaError_t e, const char *what) {
 int dev_alloc(pasur_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
-        return set_err(ctx, PASUR_ENOMEM, "device-memory budget exceeded (" + std::to_string(ctx->in_use + bytes) + " > " +
-                                              std::to_string(ctx->budget) + " bytes)");
+    pasur_ctx *a = ctx->acct ? ctx->acct : ctx;
+    {
+        std::lock_guard<std::mutex> lk(a->acct_mu);
+        if (a->budget && a->in_use + bytes > a->budget)
+            return set_err(ctx, PASUR_ENOMEM, "device-memory budget exceeded (" + std::to_string(a->in_use + bytes) + " > " +
+                                                  std::to_string(a->budget) + " bytes)");
+        a->in_use += bytes;
+        a->peak = std::max(a->peak, a->in_use);
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        *p = nullptr;
+        std::lock_guard<std::mutex> lk(a->acct_mu);
+        a->in_use -= std::min(a->in_use, bytes);
         return set_err(ctx, PASUR_ENOMEM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
-    ctx->in_use += bytes;
-    ctx->peak = std::max(ctx->peak, ctx->in_use);
     return PASUR_OK;
 }
 
@@ -42,7 +49,9 @@ void dev_free(pasur_ctx *ctx, void *p, size_t bytes) {
     if (!p) return;
     if (bytes == 0) bytes = 16;
     cudaFreeAsync(p, ctx->stream);
-    ctx->in_use -= std::min(ctx->in_use, bytes);
+    pasur_ctx *a = ctx->acct ? ctx->acct : ctx;
+    std::lock_guard<std::mutex> lk(a->acct_mu);
+    a->in_use -= std::min(a->in_use, bytes);
 }
 
 int tree_alloc(pasur_tree *t, void **p, size_t bytes) {

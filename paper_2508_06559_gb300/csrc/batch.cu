@@ -5,10 +5,15 @@
 // CFR, root utilities, round 5 down to the first round) is captured once into a CUDA graph and
 // replayed.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 
 #include "pasur_internal.cuh"
 
@@ -52,6 +57,147 @@ int batch_alloc(pasur_batch *b, void **p, size_t bytes) {
     PASUR_TRY(dev_alloc(b->ctx, p, bytes));
     b->owned.push_back({*p, bytes});
     return PASUR_OK;
+}
+
+// What one deal leaves for the merged plans: per round its work items by launch class, the
+// shared memory each class needs and its cluster items.
+struct DealPlan {
+    std::vector<CfrItem> own[6][8];
+    size_t need[6][8] = {};
+    std::vector<ClusterItem> clu[6];
+    int64_t edges = 0;
+};
+
+// One deal on the context wc: its rounds forward from the standalone convention root (pool
+// deck[0:4], score 0), each tree unfolded and linked to the next, then every tree's CFR layout.
+int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, DealPlan &o) {
+    uint64_t pool0 = 0;
+    for (int i = 0; i < 4; i++) pool0 |= 1ULL << deck[i];
+    std::vector<uint64_t> pools(1, pool0);
+    std::vector<int64_t> soff = {0, 1};
+    std::vector<pasur_score> scores(1, pasur_score{0, 0, 0, 0});
+    for (int ri = 0; ri < b->n_rounds; ri++) {
+        pasur_tree *t = nullptr;
+        PASUR_TRY(pasur_build_round(wc, deck, b->first_round + ri, pools.data(), (int64_t)pools.size(), &t));
+        b->trees[(size_t)(d * b->n_rounds + ri)] = t;
+        PASUR_TRY(pasur_unfold(t, soff.data(), scores.data(), nullptr));
+        PASUR_TRY(tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(t->Q[8] + 1)));
+        PASUR_TRY(tree_alloc(t, (void **)&b->util[(size_t)(d * b->n_rounds + ri)], sizeof(float) * (size_t)(t->Q[0] + 1)));
+        if (t->M[8] > 0) PASUR_CUDA(wc, cudaMemsetAsync(t->leaf_v, 0, sizeof(float) * (size_t)(t->Q[8] + 1), wc->stream));
+        if (b->first_round + ri < 5) {
+            int64_t np = 0, nr = 0;
+            PASUR_TRY(pasur_next_roots(t, nullptr, 0, nullptr, nullptr, 0, nullptr, &np, &nr));
+            pools.assign((size_t)np, 0);
+            soff.assign((size_t)np + 1, 0);
+            scores.assign((size_t)nr, pasur_score{});
+            PASUR_TRY(pasur_next_roots(t, pools.data(), np, soff.data(), scores.data(), nr, nullptr, &np, &nr));
+        }
+    }
+    for (int ri = 0; ri < b->n_rounds; ri++) {
+        pasur_tree *t = tree_of(b, d, ri);
+        PASUR_TRY(cfr_setup_tree(t, &b->cfg, (int)d, o.own[ri], o.need[ri], &o.clu[ri]));
+        t->cfr_ready = true;
+        t->variant = b->cfg.variant;
+        // the tree keeps its own items for exporting its average strategy
+        t->plan.items_h.clear();
+        for (int c = 0; c < 8; c++) t->plan.items_h.insert(t->plan.items_h.end(), o.own[ri][c].begin(), o.own[ri][c].end());
+        t->plan.n_items = (int64_t)t->plan.items_h.size();
+        if (t->plan.n_items) {
+            PASUR_TRY(tree_alloc(t, (void **)&t->plan.items_d, sizeof(CfrItem) * (size_t)t->plan.n_items));
+            PASUR_CUDA(wc, cudaMemcpyAsync(t->plan.items_d, t->plan.items_h.data(), sizeof(CfrItem) * (size_t)t->plan.n_items,
+                                           cudaMemcpyHostToDevice, wc->stream));
+        }
+        for (int k = 1; k < 9; k++) o.edges += t->Q[k];
+    }
+    PASUR_CUDA(wc, cudaStreamSynchronize(wc->stream));
+    return PASUR_OK;
+}
+
+// A build worker's context: its own stream, work counter and error word on the parent's device,
+// the parent's capture table, allocations charged to the parent.
+int open_worker(pasur_ctx *parent, pasur_ctx *w) {
+    w->device = parent->device;
+    w->num_sms = parent->num_sms;
+    w->smem_optin = parent->smem_optin;
+    w->tab = parent->tab;
+    w->tab_off = parent->tab_off;
+    w->acct = parent;
+    PASUR_CUDA(w, cudaSetDevice(w->device));
+    PASUR_CUDA(w, cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+    w->own_stream = true;
+    PASUR_TRY(dev_alloc(w, (void **)&w->counter, 64));
+    PASUR_TRY(dev_alloc(w, (void **)&w->errflag, 64));
+    PASUR_CUDA(w, cudaMemsetAsync(w->errflag, 0, 64, w->stream));
+    return PASUR_OK;
+}
+
+void close_worker(pasur_ctx *w) {
+    dev_free(w, w->counter, 64);
+    dev_free(w, w->errflag, 64);
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    if (w->own_stream) cudaStreamDestroy(w->stream);
+}
+
+// Build every deal, spread over up to 8 host threads, each on a context with its own stream so
+// that the many small launches and synchronisations of different deals overlap.  Deals are taken
+// in order from a shared counter; what each produces depends only on the deal, and the trees are
+// handed to the batch's context afterwards.  PASUR_BUILD_WORKERS sets the number of threads.
+int build_deals(pasur_batch *b, const uint8_t *decks, std::vector<DealPlan> &dp, int *n_used) {
+    pasur_ctx *ctx = b->ctx;
+    int nw = (int)std::min<int64_t>(b->n_deals, 8);
+    const unsigned hw = std::thread::hardware_concurrency();
+    if (hw > 0) nw = std::min<int>(nw, (int)hw);
+    if (const char *e = getenv("PASUR_BUILD_WORKERS")) nw = std::max(1, std::min(nw, atoi(e)));
+    *n_used = nw;
+    if (nw <= 1) {
+        for (int64_t d = 0; d < b->n_deals; d++) PASUR_TRY(build_deal(b, ctx, decks + 52 * d, d, dp[(size_t)d]));
+        return PASUR_OK;
+    }
+    std::vector<std::unique_ptr<pasur_ctx>> ws;
+    int rc = PASUR_OK;
+    for (int i = 0; i < nw && rc == PASUR_OK; i++) {
+        ws.emplace_back(new pasur_ctx());
+        rc = open_worker(ctx, ws.back().get());
+        if (rc != PASUR_OK) ctx->err = "pasur_batch_create: build worker: " + ws.back()->err;
+    }
+    std::atomic<int64_t> next{0};
+    std::atomic<bool> failed{false};
+    std::mutex mu;
+    int64_t err_deal = -1;
+    int err_rc = PASUR_OK;
+    std::string err_msg;
+    auto run = [&](pasur_ctx *w) {
+        cudaSetDevice(w->device);
+        for (;;) {
+            const int64_t d = next.fetch_add(1);
+            if (d >= b->n_deals || failed.load()) return;
+            const int r = build_deal(b, w, decks + 52 * d, d, dp[(size_t)d]);
+            if (r != PASUR_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (err_deal < 0 || d < err_deal) err_deal = d, err_rc = r, err_msg = w->err;
+                failed.store(true);
+                return;
+            }
+        }
+    };
+    if (rc == PASUR_OK) {
+        std::vector<std::thread> th;
+        for (auto &w : ws) th.emplace_back(run, w.get());
+        for (auto &x : th) x.join();
+    }
+    // the trees (built or partly built) belong to the batch's context from here on
+    for (pasur_tree *t : b->trees)
+        if (t) t->ctx = ctx;
+    for (auto &w : ws) {
+        ctx->live_trees += w->live_trees;
+        ctx->launches += w->launches;
+        close_worker(w.get());
+    }
+    if (rc == PASUR_OK && err_deal >= 0) {
+        ctx->err = "deal " + std::to_string(err_deal) + ": " + err_msg;
+        rc = err_rc;
+    }
+    return rc;
 }
 
 // Time one class of a plan alone for a few iterations at each candidate block size; keep the best.
@@ -213,36 +359,24 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
     b->trees.assign((size_t)(n_deals * b->n_rounds), nullptr);
     b->util.assign(b->trees.size(), nullptr);
     int rc = PASUR_OK;
-    // forward: every deal's rounds from the standalone convention root (pool deck[0:4], score 0)
-    for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
-        const uint8_t *deck = decks + 52 * d;
-        uint64_t pool0 = 0;
-        for (int i = 0; i < 4; i++) pool0 |= 1ULL << deck[i];
-        std::vector<uint64_t> pools(1, pool0);
-        std::vector<int64_t> soff = {0, 1};
-        std::vector<pasur_score> scores(1, pasur_score{0, 0, 0, 0});
-        for (int ri = 0; ri < b->n_rounds && rc == PASUR_OK; ri++) {
-            pasur_tree *t = nullptr;
-            rc = pasur_build_round(ctx, deck, first_round + ri, pools.data(), (int64_t)pools.size(), &t);
-            if (rc != PASUR_OK) break;
-            b->trees[(size_t)(d * b->n_rounds + ri)] = t;
-            rc = pasur_unfold(t, soff.data(), scores.data(), nullptr);
-            if (rc == PASUR_OK) rc = tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(t->Q[8] + 1));
-            if (rc == PASUR_OK) rc = tree_alloc(t, (void **)&b->util[(size_t)(d * b->n_rounds + ri)], sizeof(float) * (size_t)(t->Q[0] + 1));
-            if (rc == PASUR_OK && t->M[8] > 0)
-                rc = cudaMemsetAsync(t->leaf_v, 0, sizeof(float) * (size_t)(t->Q[8] + 1), ctx->stream) == cudaSuccess ? PASUR_OK : PASUR_ECUDA;
-            if (rc == PASUR_OK && first_round + ri < 5) {
-                int64_t np = 0, nr = 0;
-                rc = pasur_next_roots(t, nullptr, 0, nullptr, nullptr, 0, nullptr, &np, &nr);
-                if (rc == PASUR_OK) {
-                    pools.assign((size_t)np, 0);
-                    soff.assign((size_t)np + 1, 0);
-                    scores.assign((size_t)nr, pasur_score{});
-                    rc = pasur_next_roots(t, pools.data(), np, soff.data(), scores.data(), nr, nullptr, &np, &nr);
-                }
-            }
-        }
-    }
+    const bool verbose = getenv("PASUR_VERBOSE") != nullptr;
+    using clk = std::chrono::steady_clock;
+    double ph_ms[4] = {0};  // rounds and layouts, surrogate, merged plans, autotune
+    int n_workers = 1;
+    auto lap = [&](clk::time_point &t0, int i) {
+        if (!verbose) return;
+        cudaStreamSynchronize(ctx->stream);
+        const clk::time_point t1 = clk::now();
+        ph_ms[i] += std::chrono::duration<double, std::milli>(t1 - t0).count();
+        t0 = t1;
+    };
+    clk::time_point tp = clk::now();
+    // every deal's rounds and CFR layouts, deals spread over the build workers
+    std::vector<DealPlan> dp((size_t)n_deals);
+    rc = ensure_capture_table(ctx);
+    if (rc == PASUR_OK) rc = cudaStreamSynchronize(ctx->stream) == cudaSuccess ? PASUR_OK : set_err(ctx, PASUR_ECUDA, "pasur_batch_create: sync");
+    if (rc == PASUR_OK) rc = build_deals(b, decks, dp, &n_workers);
+    lap(tp, 0);
     // surrogate values of every deal's roots after the last round
     if (rc == PASUR_OK && last_round < 5) {
         b->cut_util.assign((size_t)n_deals, nullptr);
@@ -253,43 +387,31 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
                 rc = pasur_mlp_predict_next(mlp, t, b->cut_util[(size_t)d], t->n_next_roots);
         }
     }
-    // CFR layouts and one merged plan per round
+    lap(tp, 1);
+    // one merged plan per round, the deals' items in deal order
     b->plans.resize((size_t)b->n_rounds);
     for (int ri = 0; ri < b->n_rounds && rc == PASUR_OK; ri++) {
         std::vector<CfrItem> cls_items[8];
         size_t need[8] = {0};
         std::vector<TreeView> views;
         std::vector<ClusterItem> clu;
-        for (int64_t d = 0; d < n_deals && rc == PASUR_OK; d++) {
-            pasur_tree *t = tree_of(b, d, ri);
-            std::vector<CfrItem> own[8];
-            rc = cfr_setup_tree(t, cfg, (int)d, own, need, &clu);
-            if (rc != PASUR_OK) break;
-            t->cfr_ready = true;
-            t->variant = cfg->variant;
-            // the tree keeps its own items for exporting its average strategy
-            t->plan.items_h.clear();
+        for (int64_t d = 0; d < n_deals; d++) {
+            DealPlan &o = dp[(size_t)d];
             for (int c = 0; c < 8; c++) {
-                t->plan.items_h.insert(t->plan.items_h.end(), own[c].begin(), own[c].end());
-                cls_items[c].insert(cls_items[c].end(), own[c].begin(), own[c].end());
+                cls_items[c].insert(cls_items[c].end(), o.own[ri][c].begin(), o.own[ri][c].end());
+                need[c] = std::max(need[c], o.need[ri][c]);
             }
-            t->plan.n_items = (int64_t)t->plan.items_h.size();
-            if (t->plan.n_items) {
-                rc = tree_alloc(t, (void **)&t->plan.items_d, sizeof(CfrItem) * (size_t)t->plan.n_items);
-                if (rc == PASUR_OK &&
-                    cudaMemcpyAsync(t->plan.items_d, t->plan.items_h.data(), sizeof(CfrItem) * (size_t)t->plan.n_items,
-                                    cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-                    rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_create: copy items");
-            }
-            views.push_back(t->view);
-            b->edges += t->Q[1] + t->Q[2] + t->Q[3] + t->Q[4] + t->Q[5] + t->Q[6] + t->Q[7] + t->Q[8];
+            clu.insert(clu.end(), o.clu[ri].begin(), o.clu[ri].end());
+            views.push_back(tree_of(b, d, ri)->view);
         }
-        if (rc == PASUR_OK)
-            rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu);
+        rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu);
     }
+    for (const DealPlan &o : dp) b->edges += o.edges;
+    lap(tp, 2);
     if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
     if (rc == PASUR_OK && b->dcfr) b->owned.push_back({b->dcfr, b->dcfr_bytes});
     if (rc == PASUR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "pasur_batch_create: sync");
+    lap(tp, 2);
     // autotune the block size of every class on the round with the most work
     if (rc == PASUR_OK && cfg->threads == 0) {
         int big = 0;
@@ -302,7 +424,12 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
         rc = autotune(b, b->plans[(size_t)big]);
     }
     if (rc == PASUR_OK) rc = ensure_aux(ctx);
-    if (rc == PASUR_OK && getenv("PASUR_VERBOSE")) rc = print_batch(b);
+    lap(tp, 3);
+    if (rc == PASUR_OK && verbose) {
+        fprintf(stderr, "[pasur] batch create: rounds and layouts %.1f ms (%d build workers), surrogate %.1f, "
+                        "merged plans %.1f, autotune %.1f\n", ph_ms[0], n_workers, ph_ms[1], ph_ms[2], ph_ms[3]);
+        rc = print_batch(b);
+    }
     if (rc != PASUR_OK) {
         free_batch(b);
         delete b;

@@ -301,12 +301,18 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev) {
         int64_t m1 = 0;
         PASUR_TRY(read_i64(ctx, t->child_off[k] + m, &m1));
         t->M[k + 1] = m1;
-        size_t cap = (size_t)m1 + 1;
-        PASUR_TRY(tree_alloc(t, (void **)&t->st[k + 1], sizeof(GTState) * cap));
-        PASUR_TRY(tree_alloc(t, (void **)&t->parent[k + 1], sizeof(int64_t) * cap));
-        PASUR_TRY(tree_alloc(t, (void **)&t->lay[k + 1], sizeof(int8_t) * cap));
-        PASUR_TRY(tree_alloc(t, (void **)&t->pick[k + 1], sizeof(uint64_t) * cap));
-        PASUR_TRY(tree_alloc(t, (void **)&t->root[k + 1], sizeof(int32_t) * cap));
+        // the level's five arrays in one allocation, each piece 256-byte aligned
+        const size_t cap = (size_t)m1 + 1;
+        auto piece = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t b_st = piece(sizeof(GTState) * cap), b_par = piece(sizeof(int64_t) * cap),
+                     b_lay = piece(sizeof(int8_t) * cap), b_pick = piece(sizeof(uint64_t) * cap);
+        char *lv = nullptr;
+        PASUR_TRY(tree_alloc(t, (void **)&lv, b_st + b_par + b_lay + b_pick + piece(sizeof(int32_t) * cap)));
+        t->st[k + 1] = (GTState *)lv;
+        t->parent[k + 1] = (int64_t *)(lv + b_st);
+        t->lay[k + 1] = (int8_t *)(lv + b_st + b_par);
+        t->pick[k + 1] = (uint64_t *)(lv + b_st + b_par + b_lay);
+        t->root[k + 1] = (int32_t *)(lv + b_st + b_par + b_lay + b_pick);
         if (m > 0) {
             EmitOut o{t->st[k + 1], t->parent[k + 1], t->lay[k + 1], t->pick[k + 1], t->root[k + 1]};
             k_expand<true><<<grid_for(m * 32, 256), 256, 0, ctx->stream>>>(t->st[k], m, mover, t->final_round, ctx->tab,
@@ -352,23 +358,26 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev) {
 
 int unfold_levels(pasur_tree *t) {
     pasur_ctx *ctx = t->ctx;
-    for (int k = 0; k < 9; k++) {
+    int64_t mmax = 0;
+    for (int k = 0; k < 9; k++) mmax = std::max(mmax, t->M[k]);
+    // one slot-count buffer serves every level (the levels run in stream order)
+    int64_t *slots = nullptr;
+    const size_t sb = sizeof(int64_t) * (size_t)(mmax + 1);
+    PASUR_TRY(dev_alloc(ctx, (void **)&slots, sb));
+    int rc = PASUR_OK;
+    for (int k = 0; k < 9 && rc == PASUR_OK; k++) {
         int64_t m = t->M[k];
-        if (!t->fgt_off[k]) PASUR_TRY(tree_alloc(t, (void **)&t->fgt_off[k], sizeof(int64_t) * (size_t)(m + 1)));
-        int64_t *slots = nullptr;
-        size_t sb = sizeof(int64_t) * (size_t)(m + 1);
-        PASUR_TRY(dev_alloc(ctx, (void **)&slots, sb));
-        if (m > 0) {
+        if (!t->fgt_off[k]) rc = tree_alloc(t, (void **)&t->fgt_off[k], sizeof(int64_t) * (size_t)(m + 1));
+        if (rc == PASUR_OK && m > 0) {
             k_slots_per_node<<<grid_for(m, 256), 256, 0, ctx->stream>>>(t->root[k], m, t->score_off_d, slots);
             ctx->launches++;
-            PASUR_CUDA(ctx, cudaGetLastError());
+            if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_slots_per_node launch");
         }
-        int rc = exclusive_scan_i64(ctx, slots, t->fgt_off[k], m);
-        dev_free(ctx, slots, sb);
-        if (rc != PASUR_OK) return rc;
-        PASUR_TRY(read_i64(ctx, t->fgt_off[k] + m, &t->Q[k]));
+        if (rc == PASUR_OK) rc = exclusive_scan_i64(ctx, slots, t->fgt_off[k], m);
+        if (rc == PASUR_OK) rc = read_i64(ctx, t->fgt_off[k] + m, &t->Q[k]);
     }
-    return PASUR_OK;
+    dev_free(ctx, slots, sb);
+    return rc;
 }
 
 // leaf values without any host synchronisation (the batch solver captures this in a CUDA graph);

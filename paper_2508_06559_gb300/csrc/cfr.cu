@@ -796,13 +796,24 @@ unsigned grid_for(int64_t threads, int block) {
     return (unsigned)b;
 }
 
-template <typename T>
-int tmp_alloc(pasur_ctx *ctx, std::vector<std::pair<void *, size_t>> &tmp, T **p, int64_t n) {
-    size_t b = sizeof(T) * (size_t)(n + 1);
-    PASUR_TRY(dev_alloc(ctx, (void **)p, b));
-    tmp.push_back({(void *)*p, b});
-    return PASUR_OK;
-}
+// Several device temporaries carved from one allocation (pieces 256-byte aligned, n + 1 elements
+// each): one allocator call instead of one per array.
+struct Slab {
+    size_t total = 0;
+    std::vector<std::pair<void **, size_t>> want;
+    template <typename T>
+    void add(T **p, int64_t n) {
+        want.push_back({(void **)p, total});
+        total += (sizeof(T) * (size_t)(n + 1) + 255) & ~(size_t)255;
+    }
+    int alloc(pasur_ctx *ctx, std::vector<std::pair<void *, size_t>> &tmp) {
+        char *base = nullptr;
+        PASUR_TRY(dev_alloc(ctx, (void **)&base, total));
+        tmp.push_back({(void *)base, total});
+        for (auto &w : want) *w.first = base + w.second;
+        return PASUR_OK;
+    }
+};
 
 int build_layout(pasur_tree *t) {
     pasur_ctx *ctx = t->ctx;
@@ -817,12 +828,19 @@ int build_layout(pasur_tree *t) {
     uint8_t *chain[9];
     int32_t *local[9], *active[9];
     int64_t *lrank[9], *arank[9];
-    for (int k = 0; k < 9; k++) {
-        PASUR_TRY(tmp_alloc(ctx, tmp, &chain[k], t->M[k]));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &local[k], t->M[k]));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &active[k], t->M[k]));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &lrank[k], t->M[k]));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &arank[k], t->M[k]));
+    int64_t *ranks = nullptr;
+    const int64_t nr = t->n_roots;
+    {
+        Slab sl;
+        for (int k = 0; k < 9; k++) {
+            sl.add(&chain[k], t->M[k]);
+            sl.add(&local[k], t->M[k]);
+            sl.add(&active[k], t->M[k]);
+            sl.add(&lrank[k], t->M[k]);
+            sl.add(&arank[k], t->M[k]);
+        }
+        sl.add(&ranks, 18 * (nr + 1));
+        PASUR_TRY(sl.alloc(ctx, tmp));
     }
     PASUR_CUDA(ctx, cudaMemsetAsync(chain[8], 1, (size_t)t->M[8] + 1, ctx->stream));
     for (int k = 7; k >= 0; k--) {
@@ -842,9 +860,6 @@ int build_layout(pasur_tree *t) {
         PASUR_TRY(exclusive_scan_i32(ctx, local[k], lrank[k], t->M[k]));
         PASUR_TRY(exclusive_scan_i32(ctx, active[k], arank[k], t->M[k]));
     }
-    int64_t nr = t->n_roots;
-    int64_t *ranks = nullptr;
-    PASUR_TRY(tmp_alloc(ctx, tmp, &ranks, 18 * (nr + 1)));
     RankPtrs rp;
     for (int k = 0; k < 9; k++) {
         rp.loc[k] = lrank[k];
@@ -893,8 +908,18 @@ int build_layout(pasur_tree *t) {
     PASUR_TRY(tree_alloc(t, (void **)&t->act_gt, sizeof(int64_t) * (size_t)(act_off + 1)));
     uint64_t *act_key = nullptr;
     int64_t *perm = nullptr;
-    PASUR_TRY(tmp_alloc(ctx, tmp, &act_key, act_off));
-    PASUR_TRY(tmp_alloc(ctx, tmp, &perm, act_off));
+    int32_t *t32 = nullptr;
+    uint16_t *t16 = nullptr;
+    int64_t *t64 = nullptr;
+    {
+        Slab sl;
+        sl.add(&act_key, act_off);
+        sl.add(&perm, act_off);
+        sl.add(&t32, act_off);
+        sl.add(&t16, act_off);
+        sl.add(&t64, act_off);
+        PASUR_TRY(sl.alloc(ctx, tmp));
+    }
     ChildPtrs co;
     for (int k = 0; k < 8; k++) co.p[k] = t->child_off[k];
     co.p[8] = nullptr;
@@ -921,12 +946,6 @@ int build_layout(pasur_tree *t) {
         int bits = 16;
         while (((int64_t)1 << (bits - 16)) <= act_off) bits++;
         PASUR_TRY(radix_sort_pairs(ctx, act_key, perm, act_off, bits));
-        int32_t *t32 = nullptr;
-        uint16_t *t16 = nullptr;
-        int64_t *t64 = nullptr;
-        PASUR_TRY(tmp_alloc(ctx, tmp, &t32, act_off));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &t16, act_off));
-        PASUR_TRY(tmp_alloc(ctx, tmp, &t64, act_off));
         int32_t *arr32[3] = {t->act_li, t->act_pl, t->act_cs};
         for (int i = 0; i < 3; i++) {
             k_gather<int32_t><<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(arr32[i], perm, act_off, t32);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -137,6 +138,10 @@ struct pasur_ctx {
     bool cfr_smem_raised = false;  // CFR kernels' dynamic shared-memory limit raised
     float selfplay_ms = 0.f;     // device time of the last self-play launch
     int64_t selfplay_games = 0;  //   and its number of games
+    // a batch's build workers each own a context with its own stream and error word; their
+    // allocations are charged to (and limited by the budget of) the parent context
+    pasur_ctx *acct = nullptr;
+    std::mutex acct_mu;
 };
 
 struct RootInfo {             // one GT root's subtree, level by level
