@@ -28,9 +28,11 @@ namespace pasur {
 namespace {
 
 // shared-memory classes of the resident items: budget per block (several blocks per SM), then
-// the global-memory fallback
+// the global-memory fallback.  Class 0 is sized for six 128-thread blocks per SM (228 KB per SM,
+// 1 KB reserved per block, under 0.4 KB of static shared memory; six is also the register limit
+// at 80 registers): on the full game it measured 2 % faster than 40 KB at five blocks per SM.
 constexpr int kNumCls = 6;
-constexpr size_t kClsBudget[kNumCls - 1] = {40 * 1024, 54 * 1024, 74 * 1024, 112 * 1024, 0 /* opt-in max */};
+constexpr size_t kClsBudget[kNumCls - 1] = {37536, 54 * 1024, 74 * 1024, 112 * 1024, 0 /* opt-in max */};
 constexpr int kClsGlobal = kNumCls - 1;
 constexpr int kClsCluster = 6;       // plan class of the cluster items' pseudo-items (exports only)
 constexpr int kMaxClusterCtas = 16;  // CTAs of a cluster (16: non-portable size)
@@ -350,9 +352,11 @@ __device__ __forceinline__ double iterate(const CfrParams &p, int W, const Entri
         float fpos, fneg, fs;
         dcfr_factors<VARIANT>(p, il, fpos, fneg, fs);
         run_passes<VARIANT, W1, PACKED>(0, 15, W, sh, A, R, S, V, X, sb, sn, sf, s_tu, tf, fpos, fneg, fs);
+        // the root values were written before the last step's block barrier and are next
+        // written by the last step of the next iteration
         if (tid < W) acc += (double)V[tid];
-        __syncthreads();
     }
+    __syncthreads();
     return acc;
 }
 
@@ -1437,11 +1441,10 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         owned.push_back({plan.views_d, b});
         PASUR_CUDA(ctx, cudaMemcpyAsync(plan.views_d, views.data(), b, cudaMemcpyHostToDevice, ctx->stream));
     }
-    size_t max_sm = 0;
-    for (int c = 0; c < kNumCls; c++) max_sm = std::max(max_sm, plan.cls_smem[c]);
-    if (max_sm > 48 * 1024 && !ctx->cfr_smem_raised) {
+    if (!ctx->cfr_smem_raised) {
         // the attribute is global per kernel: raise it once to the largest dynamic size any plan
         // can ask for, so that plans prepared later never lower it under an earlier plan's need
+        // (static plus dynamic shared memory above 48 KB needs it)
         size_t lim = 0;
         PASUR_TRY(cfr_dyn_smem_limit(ctx, &lim));
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
