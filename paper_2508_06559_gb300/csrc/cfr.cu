@@ -1659,10 +1659,14 @@ static void print_plan(const pasur_tree *t, const CfrPlan &plan) {
     for (int c = 0; c < kNumCls; c++) {
         int64_t n = plan.cls_end[c] - plan.cls_begin[c];
         if (!n) continue;
-        int64_t cost = 0;
-        for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) cost += plan.items_h[(size_t)i].cost;
-        fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld\n", c,
-                (long long)n, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost);
+        int64_t cost = 0, maxcost = 0;
+        for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) {
+            cost += plan.items_h[(size_t)i].cost;
+            maxcost = std::max(maxcost, plan.items_h[(size_t)i].cost);
+        }
+        fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld "
+                        "(largest item %lld)\n",
+                c, (long long)n, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost, (long long)maxcost);
     }
     for (int b = 0; b < 3; b++)
         if (plan.clu_end[b] != plan.clu_begin[b])
@@ -1722,7 +1726,9 @@ int cfr_run(pasur_tree *t, const pasur_config *cfg) {
     if (getenv("PASUR_VERBOSE")) {
         fprintf(stderr, "[pasur] round %d: %d iterations in %.3f ms (", t->round, cfg->iters, ms);
         for (int c = 0; c < kNumCls; c++) fprintf(stderr, "%s%.2f", c ? " " : "", t->plan.cls_ms[c]);
-        fprintf(stderr, " ms per class)\n");
+        fprintf(stderr, " ms per class; clusters");
+        for (int b = 0; b < 3; b++) fprintf(stderr, " %.2f", t->plan.cls_ms[kClsCluster + b]);
+        fprintf(stderr, " ms)\n");
     }
     if (ef) return set_err(ctx, PASUR_ENUMERIC, "non-finite root value in the CFR sweep");
     return PASUR_OK;
