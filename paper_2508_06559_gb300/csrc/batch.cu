@@ -200,15 +200,17 @@ int build_deals(pasur_batch *b, const uint8_t *decks, std::vector<DealPlan> &dp,
     return rc;
 }
 
-// Time one class of a plan alone for a few iterations at each candidate block size; keep the best.
+// Time one class of a plan alone (no other class, no cluster item) for a few iterations at each
+// candidate block size; keep the best.  Classes 6 and up (cluster items) have no block size to
+// choose.
 int autotune(pasur_batch *b, CfrPlan &plan) {
     pasur_ctx *ctx = b->ctx;
     pasur_config cfg = b->cfg;
-    cfg.iters = 4;
+    cfg.iters = 8;
     cudaEvent_t e0, e1;
     PASUR_CUDA(ctx, cudaEventCreate(&e0));
     PASUR_CUDA(ctx, cudaEventCreate(&e1));
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < 6; c++) {
         if (plan.cls_end[c] == plan.cls_begin[c]) continue;
         const int def = plan.cls_threads[c];
         const int cand_small[3] = {64, 128, 256}, cand_wide[3] = {256, 512, 1024};
@@ -216,6 +218,7 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
         CfrPlan one = plan;
         for (int o = 0; o < 8; o++)
             if (o != c) one.cls_begin[o] = one.cls_end[o] = 0;
+        for (int o = 0; o < 3; o++) one.clu_begin[o] = one.clu_end[o] = 0;
         float best_ms = 1e30f;
         int best = def;
         for (int i = 0; i < 3; i++) {
@@ -230,6 +233,9 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
             PASUR_CUDA(ctx, cudaEventSynchronize(e1));
             float ms = 0.f;
             PASUR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (getenv("PASUR_VERBOSE"))
+                fprintf(stderr, "[pasur] autotune class %d alone: %d blocks x %d threads, %d iterations in %.3f ms\n", c, blocks,
+                        cand[i], cfg.iters, ms);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = cand[i];

@@ -36,7 +36,9 @@ constexpr size_t kClsBudget[kNumCls - 1] = {37536, 54 * 1024, 74 * 1024, 112 * 1
 constexpr int kClsGlobal = kNumCls - 1;
 constexpr int kClsCluster = 6;       // plan class of the cluster items' pseudo-items (exports only)
 constexpr int kMaxClusterCtas = 16;  // CTAs of a cluster (16: non-portable size)
-constexpr int kClsThreads[kNumCls] = {128, 128, 256, 512, 1024, 1024};
+// default block size per class (the batch autotuner measures its own); class 3 at two 256-thread
+// blocks per SM measured faster than one 512-thread block of the 512-thread instantiation
+constexpr int kClsThreads[kNumCls] = {128, 128, 256, 256, 1024, 1024};
 
 struct CfrParams {
     const CfrItem *items;
@@ -465,6 +467,15 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrPara
         if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
         else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
     }
+}
+
+// The instantiation for blocks of `threads` threads: up to 256 threads at up to 80 registers
+// (three 256-thread blocks per SM), up to 512 at up to 128 (no spills), up to 1024 at 64 (the
+// register file of one SM).
+const void *cfr_kernel_for(int variant, int threads) {
+    if (threads <= 256) return variant == 1 ? (const void *)k_cfr_items<1, 256> : (const void *)k_cfr_items<0, 256>;
+    if (threads <= 512) return variant == 1 ? (const void *)k_cfr_items<1, 512> : (const void *)k_cfr_items<0, 512>;
+    return variant == 1 ? (const void *)k_cfr_items<1, 1024> : (const void *)k_cfr_items<0, 1024>;
 }
 
 // ---- a root subtree split over a thread-block cluster ------------------------------------------
@@ -1198,6 +1209,10 @@ int cfr_dyn_smem_limit(pasur_ctx *ctx, size_t *limit) {
     st = std::max(st, fa.sharedSizeBytes);
     PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<1, 256>));
     st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<0, 512>));
+    st = std::max(st, fa.sharedSizeBytes);
+    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<1, 512>));
+    st = std::max(st, fa.sharedSizeBytes);
     PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<0, 1024>));
     st = std::max(st, fa.sharedSizeBytes);
     PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_items<1, 1024>));
@@ -1447,10 +1462,9 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         // (static plus dynamic shared memory above 48 KB needs it)
         size_t lim = 0;
         PASUR_TRY(cfr_dyn_smem_limit(ctx, &lim));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
-        PASUR_CUDA(ctx, cudaFuncSetAttribute(k_cfr_items<1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        for (int v = 0; v < 2; v++)
+            for (int t : {256, 512, 1024})
+                PASUR_CUDA(ctx, cudaFuncSetAttribute(cfr_kernel_for(v, t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
         ctx->cfr_smem_raised = true;
     }
     for (int c = 0; c < kNumCls; c++) {
@@ -1473,10 +1487,7 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         plan.cls_threads[c] = threads;
         if (n == 0) continue;
         int per_sm = 0;
-        if (threads <= 256)
-            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, plan.cls_smem[c]));
-        else
-            PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, plan.cls_smem[c]));
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads), threads, plan.cls_smem[c]));
         if (per_sm < 1) return set_err(ctx, PASUR_EINVAL, "CFR kernel cannot be resident with this shared-memory plan");
         plan.cls_blocks[c] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n));
     }
@@ -1485,10 +1496,7 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
 
 int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks) {
     int per_sm = 0;
-    if (threads <= 256)
-        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 256>, threads, smem));
-    else
-        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cfr_items<0, 1024>, threads, smem));
+    PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads), threads, smem));
     *blocks = per_sm < 1 ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n_items));
     return PASUR_OK;
 }
@@ -1546,17 +1554,10 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
         p.i_begin = plan.cls_begin[c];
         p.i_end = plan.cls_end[c];
         p.counter = ctx->counter + c;
-        const bool wide = plan.cls_threads[c] > 256;
-        if (cfg->variant == 1 && wide)
-            k_cfr_items<1, 1024><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
-        else if (cfg->variant == 1)
-            k_cfr_items<1, 256><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
-        else if (wide)
-            k_cfr_items<0, 1024><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
-        else
-            k_cfr_items<0, 256><<<plan.cls_blocks[c], plan.cls_threads[c], plan.cls_smem[c], st>>>(p);
+        void *args[] = {&p};
+        PASUR_CUDA(ctx, cudaLaunchKernel(cfr_kernel_for(cfg->variant, plan.cls_threads[c]), dim3((unsigned)plan.cls_blocks[c]),
+                                         dim3((unsigned)plan.cls_threads[c]), args, plan.cls_smem[c], st));
         ctx->launches++;
-        PASUR_CUDA(ctx, cudaGetLastError());
         PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
         PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
         PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
