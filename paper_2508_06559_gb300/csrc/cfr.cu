@@ -100,9 +100,11 @@ __device__ __forceinline__ void td_node(int c, int sh, int w, float own, const f
     }
     const float sum = tree_sum<D>(rp);
     const bool pos = sum > 0.f;
-    const float scale = pos ? own * rcp_pos(sum) : 0.f, u = own * (1.f / (float)D);
+    // pos: rp * scale (an fma with a zero addend rounds the product alone); otherwise every rp is
+    // zero and the fma gives the uniform share: one instruction per child instead of two
+    const float scale = pos ? own * rcp_pos(sum) : 0.f, u = pos ? 0.f : own * (1.f / (float)D);
 #pragma unroll
-    for (int a = 0; a < D; a++) X[at<W1>(c, a, sh, w)] = pos ? rp[a] * scale : u;
+    for (int a = 0; a < D; a++) X[at<W1>(c, a, sh, w)] = __fmaf_rn(rp[a], scale, u);
 }
 
 template <bool W1>
@@ -140,11 +142,11 @@ __device__ __forceinline__ float bu_node(int c, int sh, int w, float pp, float s
     }
     const float sum = tree_sum<D>(rp);
     const bool pos = sum > 0.f;
-    const float inv = pos ? rcp_pos(sum) : 0.f, u = 1.f / (float)D;
+    const float inv = pos ? rcp_pos(sum) : 0.f, u = pos ? 0.f : 1.f / (float)D;
     float sg[D], dv[D];
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        sg[a] = pos ? rp[a] * inv : u;
+        sg[a] = __fmaf_rn(rp[a], inv, u);  // rp * inv, or the uniform share (as in td_node)
         dv[a] = a == 0 ? 0.f : sg[a] * (v[a] - v[0]);
     }
     const float vh = D == 1 ? v[0] : v[0] + tree_sum<D>(dv);
