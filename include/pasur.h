@@ -186,7 +186,11 @@ typedef struct pasur_batch pasur_batch;
  * unfolding and links, and plan their CFR: the work items of all deals' trees of one round are
  * merged into one persistent launch per shared-memory class (largest subtrees first).  With
  * cfg->threads == 0 an autotuner times candidate block sizes per class on the round with the most
- * work and keeps the fastest.  cfg is fixed for the batch.  The batch owns its trees. */
+ * work and keeps the fastest.  cfg is fixed for the batch.  The batch owns its trees.
+ * The deals are built on up to 8 host threads (at most one per deal and per host core; the
+ * environment variable PASUR_BUILD_WORKERS lowers the count), each on its own CUDA stream; the
+ * result does not depend on the count.  Their device memory counts against ctx's budget; on any
+ * error (the first failing deal's message in pasur_last_error) nothing of the batch is left. */
 int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const pasur_config *cfg,
                        pasur_batch **out);
 
