@@ -267,7 +267,7 @@ int pasur_root_values(pasur_tree *tree, int mode, const float *sigma, const doub
  * round-start FGT root, so that a round's leaves can take their next-round values (eq.
  * passuputil) without the later rounds being built and solved.  The paper's learned part is a
  * gradient-boosted model of the strategy (§Results); this surrogate is trained on the U values
- * the exact solver produces and uses the solver as its fallback and judge.  Weights are stored in
+ * the exact solver produces; the exact solve is its fallback and measures its error.  Weights are stored in
  * f32 (Adam state in f32) and used as bf16 by the tensor-core kernels, which accumulate in f32.
  *
  * Input features of a root of round r with pool P and score (ac, bc, delta, bonus), 256 values,
