@@ -148,10 +148,12 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
     ms, edges, launches = b.pasur_batch_stats()
     d2h = 0
     info = []
+    _BATCH_SIZES[:] = [0] * len(decks)
     for d in range(len(decks)):
         for r in range(first_round, 6):
             t = b.pasur_batch_tree(d, r)
             q = t.pasur_tree_sizes()[1]
+            _BATCH_SIZES[d] += int(q.sum())
             ne = int(q[1:].sum())
             if out_device:
                 U = torch.empty(int(q[0]), dtype=torch.float32, device="cuda")
@@ -178,6 +180,16 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
 
 
 _SUR: dict = {}
+_BATCH_SIZES: list = []  # FGT nodes of every deal of the last batched step (all solved rounds)
+
+
+def size_histogram(sizes):
+    """Spread of the deals' FGT sizes: min / median / max and a count per decade."""
+    a = np.asarray(sizes, np.float64)
+    dec = np.floor(np.log10(np.maximum(a, 1))).astype(int)
+    hist = {f"1e{k}-1e{k + 1}": int((dec == k).sum()) for k in range(int(dec.min()), int(dec.max()) + 1)}
+    return {"deals": len(a), "min": int(a.min()), "median": float(np.median(a)), "max": int(a.max()),
+            "per_decade": hist}
 
 
 def no_learning_params(P):
@@ -503,6 +515,8 @@ def run_ours(args, rank, world, dist):
                      "strategy with Philox4x64-10 (key = deal seed); inside each timed step"),
         "wall_s_timed": wall,
     }
+    if args.workload == "batch64" and _BATCH_SIZES:
+        line["config"]["fgt_nodes_per_deal"] = size_histogram(_BATCH_SIZES)
     if args.workload == "surrogate16":
         si = dict(_SUR["info"])
         si["surrogate_step_s"] = ms_per_step / 1e3
