@@ -66,6 +66,11 @@ typedef struct {
  *                over a thread-block cluster (up to 16 SMs, distributed shared memory); with
  *                split_bytes > 0 every subtree needing more than that many bytes is split too
  *                (0 = only those that do not fit).  Results do not depend on the split.
+ *   stream_bytes a root subtree that does not fit one block's shared memory and has at least 16
+ *                score slots, or fits no cluster either, is solved by a level-streaming sweep over
+ *                every SM (state in device memory, one launch per level step); with
+ *                stream_bytes > 0 every subtree needing more than that many bytes is streamed
+ *                (0 = the default rule).  Results do not depend on the path.
  */
 typedef struct {
     int32_t variant;
@@ -75,6 +80,7 @@ typedef struct {
     int32_t slots_per_item;
     int32_t threads;
     int32_t split_bytes;
+    int32_t stream_bytes;
 } pasur_config;
 
 /* Fill *cfg with the defaults: vanilla, 1000 iterations, tau = 1e-6, DCFR (1.5, 0, 2). */

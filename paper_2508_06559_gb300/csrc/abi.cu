@@ -151,6 +151,7 @@ int pasur_config_default(pasur_config *cfg) {
     cfg->slots_per_item = 0;
     cfg->threads = 0;
     cfg->split_bytes = 0;
+    cfg->stream_bytes = 0;
     return PASUR_OK;
 }
 

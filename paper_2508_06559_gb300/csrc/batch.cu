@@ -201,8 +201,8 @@ int build_deals(pasur_batch *b, const uint8_t *decks, std::vector<DealPlan> &dp,
 }
 
 // Time one class of a plan alone (no other class, no cluster item) for a few iterations at each
-// candidate block size; keep the best.  Classes 6 and up (cluster items) have no block size to
-// choose.
+// candidate block size; keep the best.  Class 5 (the level-streaming sweep) and the cluster
+// items have no block size to choose.
 int autotune(pasur_batch *b, CfrPlan &plan) {
     pasur_ctx *ctx = b->ctx;
     pasur_config cfg = b->cfg;
@@ -210,7 +210,7 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
     cudaEvent_t e0, e1;
     PASUR_CUDA(ctx, cudaEventCreate(&e0));
     PASUR_CUDA(ctx, cudaEventCreate(&e1));
-    for (int c = 0; c < 6; c++) {
+    for (int c = 0; c < 5; c++) {
         if (plan.cls_end[c] == plan.cls_begin[c]) continue;
         const int def = plan.cls_threads[c];
         const int cand_small[3] = {64, 128, 256}, cand_wide[3] = {256, 512, 1024};

@@ -61,6 +61,9 @@ __host__ __device__ __forceinline__ size_t resident_bytes(int64_t L, int64_t nA,
 }
 
 constexpr int kMaxSlots = 32;  // score slots per work item
+// a root too large for one block is streamed (class 5) rather than split over a cluster when it
+// has at least this many score slots
+constexpr int64_t kStreamMinSlots = 16;
 
 // Index of child edge a of a node whose first child is local node c, at slot w of an item of
 // 2^sh slots (slot-minor layout; every item's slot count is a power of two); W1: single-slot
@@ -468,6 +471,159 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrPara
         const CfrRoot &cr = tv.roots[it.root];
         if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
         else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
+    }
+}
+
+// ---- class 5: a level-streaming sweep over every SM --------------------------------------------
+//
+// Items whose state lives in device memory are not given one block each: every level step of an
+// iteration is one launch over the (entry, slot) pairs of that level of all such items of the
+// plan, spread over the whole grid (the launch boundary is the level barrier).  A pair runs the
+// same node code as in a block, so the results are the block sweep's bit for bit.
+
+struct StreamPlan {
+    const int64_t *pairs;  // [8][n + 1] exclusive prefix of (entry, slot) pairs per level
+    const int64_t *locs;   // [n + 1] of (local node, slot) pairs
+    const int64_t *slots;  // [n + 1] of slots
+    uint32_t *tu;          // per slot: largest |terminal value| (float bits)
+    double *acc;           // per slot: sum of the root values of the current call
+    int64_t n;
+};
+
+// j with pre[j] <= x < pre[j + 1] (pre[0] = 0 <= x < pre[n])
+__device__ __forceinline__ int64_t stream_item(const int64_t *pre, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// the prefixes of a plan's class-5 items (one thread; once per plan)
+__global__ void k_stream_plan(const CfrItem *items, int64_t n, const TreeView *views, int64_t *pairs, int64_t *locs) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t pk[8] = {0}, pl = 0;
+    for (int64_t j = 0; j < n; j++) {
+        const CfrItem it = items[j];
+        const CfrRoot &cr = views[it.tree].roots[it.root];
+        for (int k = 0; k < 8; k++) {
+            pairs[(int64_t)k * (n + 1) + j] = pk[k];
+            pk[k] += (int64_t)(cr.as[k + 1] - cr.as[k]) * it.ns;
+        }
+        locs[j] = pl;
+        pl += (int64_t)cr.ls[9] * it.ns;
+    }
+    for (int k = 0; k < 8; k++) pairs[(int64_t)k * (n + 1) + n] = pk[k];
+    locs[n] = pl;
+}
+
+// terminal values and the dead-zone scale per slot, root reach 1, sums cleared
+__global__ void k_stream_setup(CfrParams p, StreamPlan sp) {
+    const int64_t total = sp.locs[sp.n];
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = stream_item(sp.locs, sp.n, x);
+        const CfrItem it = p.items[j];
+        const TreeView &tv = p.views[it.tree];
+        const CfrRoot &cr = tv.roots[it.root];
+        const int sh = __ffs(it.ns) - 1;
+        const int64_t r = x - sp.locs[j];
+        const int li = (int)(r >> sh), w = (int)(r & (it.ns - 1));
+        float *V = tv.V + it.scratch_base, *X = tv.X + it.scratch_base;
+        const int64_t q = tv.loc_tq[cr.loc_off + li];
+        if (q >= 0) {
+            const float v = tv.leaf_v[q + it.s0 + w];
+            V[r] = v;
+            atomicMax(&sp.tu[sp.slots[j] + w], __float_as_uint(fabsf(v)));
+        }
+        if (li == 0) {
+            X[w] = 1.f;
+            sp.acc[sp.slots[j] + w] = 0.0;
+        }
+    }
+}
+
+// one level step (level k; top-down or bottom-up) of iteration il of every class-5 item
+template <int VARIANT, bool TD>
+__global__ void __launch_bounds__(256) k_stream_level(CfrParams p, StreamPlan sp, int k, int il) {
+    const int64_t *pre = sp.pairs + (int64_t)k * (sp.n + 1);
+    const int64_t total = pre[sp.n];
+    const float tf = (float)(p.t0 + il + 1);
+    float fpos, fneg, fs;
+    dcfr_factors<VARIANT>(p, il, fpos, fneg, fs);
+    const bool alex = (k & 1) == 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = stream_item(pre, sp.n, x);
+        const CfrItem it = p.items[j];
+        const TreeView &tv = p.views[it.tree];
+        const CfrRoot &cr = tv.roots[it.root];
+        const int W = it.ns, sh = __ffs(W) - 1;
+        const int64_t r = x - pre[j];
+        const int e = cr.as[k] + (int)(r >> sh), w = (int)(r & (W - 1));
+        Entries<false> G{};
+        G.li = tv.act_li + cr.act_off;
+        G.pl = tv.act_pl + cr.act_off;
+        G.cs = tv.act_cs + cr.act_off;
+        G.d = tv.act_d + cr.act_off;
+        float *R = tv.R + it.data_base, *S = tv.S + it.data_base;
+        float *V = tv.V + it.scratch_base, *X = tv.X + it.scratch_base;
+        const float thr = (p.tau * __uint_as_float(sp.tu[sp.slots[j] + w])) * tf;
+        int c, d, li, pl;
+        G.child(e, c, d);
+        G.self(e, li, pl);
+        if (TD) {
+            const float own = pl < 0 ? 1.f : X[(pl << sh) + w];
+            switch (d) {
+                case 1: td_node<1, false>(c, sh, w, own, R, X, thr); break;
+                case 2: td_node<2, false>(c, sh, w, own, R, X, thr); break;
+                case 3: td_node<3, false>(c, sh, w, own, R, X, thr); break;
+                case 4: td_node<4, false>(c, sh, w, own, R, X, thr); break;
+                case 5: td_node<5, false>(c, sh, w, own, R, X, thr); break;
+                case 6: td_node<6, false>(c, sh, w, own, R, X, thr); break;
+                case 7: td_node<7, false>(c, sh, w, own, R, X, thr); break;
+                case 8: td_node<8, false>(c, sh, w, own, R, X, thr); break;
+                default: td_node_any<false>(c, d, sh, w, own, R, X, thr);
+            }
+        } else {
+            const float pp = pl < 0 ? 1.f : X[(pl << sh) + w];
+            const float po = X[(li << sh) + w];
+            const float spo = alex ? po : -po;
+            float vh;
+            switch (d) {
+                case 1: vh = bu_node<VARIANT, 1, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 2: vh = bu_node<VARIANT, 2, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 3: vh = bu_node<VARIANT, 3, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 4: vh = bu_node<VARIANT, 4, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 5: vh = bu_node<VARIANT, 5, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 6: vh = bu_node<VARIANT, 6, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 7: vh = bu_node<VARIANT, 7, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                case 8: vh = bu_node<VARIANT, 8, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+                default: vh = bu_node_any<VARIANT, false>(c, d, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
+            }
+            V[(li << sh) + w] = vh;
+            if (k == 0) sp.acc[sp.slots[j] + w] += (double)vh;  // the root (one entry per item)
+        }
+    }
+}
+
+// the call's root values into the running sums (a root without moves keeps its terminal value)
+__global__ void k_stream_finalize(CfrParams p, StreamPlan sp) {
+    const int64_t total = sp.slots[sp.n];
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = stream_item(sp.slots, sp.n, x);
+        const CfrItem it = p.items[j];
+        const TreeView &tv = p.views[it.tree];
+        const CfrRoot &cr = tv.roots[it.root];
+        const int w = (int)(x - sp.slots[j]);
+        double acc = sp.acc[x];
+        if (cr.as[1] == cr.as[0]) {
+            const float v = tv.V[it.scratch_base + w];
+            acc = 0.0;
+            for (int il = 0; il < p.iters; il++) acc += (double)v;
+        }
+        if (!isfinite(acc)) atomicOr(p.err, 1);
+        tv.uacc[tv.fgt_off0[it.root] + it.s0 + w] += acc;
     }
 }
 
@@ -1004,10 +1160,10 @@ namespace {
 // (in GT order) into parts that each fit one block; CTA 0 also holds the top levels.  Appends the
 // pseudo-roots to croots_h, their entries and local-node leaf indices to the host vectors, and
 // the exchange entries to t->cx_h.
-int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t part_max, std::vector<SplitRoot> &splits,
-                std::vector<int32_t> &split_of, std::vector<int32_t> &nli, std::vector<int32_t> &npl,
-                std::vector<int32_t> &ncs, std::vector<uint16_t> &nd, std::vector<int64_t> &ngt,
-                std::vector<int64_t> &ntq) {
+int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t part_max, const std::vector<char> &streamed,
+                std::vector<SplitRoot> &splits, std::vector<int32_t> &split_of, std::vector<int32_t> &nli,
+                std::vector<int32_t> &npl, std::vector<int32_t> &ncs, std::vector<uint16_t> &nd,
+                std::vector<int64_t> &ngt, std::vector<int64_t> &ntq) {
     pasur_ctx *ctx = t->ctx;
     const int64_t nr = t->n_roots;
     split_of.assign((size_t)nr, -1);
@@ -1016,7 +1172,7 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
         const CfrRoot &cr = t->croots_h[(size_t)g];
         const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
-        if (Sg == 0 || L == 0 || nA < 2) continue;
+        if (Sg == 0 || L == 0 || nA < 2 || streamed[(size_t)g]) continue;
         const size_t need = resident_bytes(L, nA, 1);
         if (need > dyn_max || (cfg->split_bytes > 0 && need > (size_t)cfg->split_bytes)) cand.push_back(g);
     }
@@ -1244,9 +1400,23 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     t->croots_h.resize((size_t)t->n_roots);
     t->cparts_h.clear();
     t->cx_h.clear();
+    // roots streamed over every SM (class 5): those above cfg->stream_bytes, and those too large
+    // for one block that have enough score slots to fill the streaming sweep's warps with
+    // consecutive slots; roots that fit neither a block nor a cluster reach class 5 below too
+    std::vector<char> streamed((size_t)t->n_roots, 0);
+    for (int64_t g = 0; g < t->n_roots; g++) {
+        const CfrRoot &cr = t->croots_h[(size_t)g];
+        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t L = cr.ls[9], nA = cr.as[9];
+        if (Sg == 0 || L == 0) continue;
+        const size_t need = resident_bytes(L, nA, 1);
+        streamed[(size_t)g] = (cfg->stream_bytes > 0 && need > (size_t)cfg->stream_bytes) ||
+                              (need > dyn_max && Sg >= kStreamMinSlots);
+    }
     size_t dyn_cl = 0;
     PASUR_TRY(cfr_cluster_smem_limit(ctx, &dyn_cl));
-    PASUR_TRY(plan_splits(t, cfg, dyn_max, std::min(dyn_max, dyn_cl), splits, split_of, nli, npl, ncs, nd, ngt, ntq));
+    PASUR_TRY(plan_splits(t, cfg, dyn_max, std::min(dyn_max, dyn_cl), streamed, splits, split_of, nli, npl, ncs, nd, ngt,
+                          ntq));
     int64_t data = 0, scratch = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         CfrRoot &cr = t->croots_h[(size_t)g];
@@ -1290,7 +1460,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
             continue;
         }
         int cls = kClsGlobal;
-        for (int c = 0; c < kNumCls - 1; c++)
+        for (int c = 0; c < kNumCls - 1 && !streamed[(size_t)g]; c++)
             if (resident_bytes(L, nA, 1) <= budget[c]) {
                 cls = c;
                 break;
@@ -1406,6 +1576,7 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
     if (cfg->threads < 0 || cfg->threads > 1024 || cfg->threads % 32)
         return set_err(ctx, PASUR_EINVAL, "cfg.threads must be 0 or a multiple of 32 <= 1024");
     if (cfg->split_bytes < 0) return set_err(ctx, PASUR_EINVAL, "cfg.split_bytes must be >= 0");
+    if (cfg->stream_bytes < 0) return set_err(ctx, PASUR_EINVAL, "cfg.stream_bytes must be >= 0");
     plan.items_h.clear();
     // classes 0..5 are launched by k_cfr_items; class 6 holds the cluster items' pseudo-items
     for (int c = 0; c <= kClsCluster; c++) {
@@ -1457,6 +1628,31 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         PASUR_TRY(dev_alloc(ctx, (void **)&plan.views_d, b));
         owned.push_back({plan.views_d, b});
         PASUR_CUDA(ctx, cudaMemcpyAsync(plan.views_d, views.data(), b, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    // class 5 runs as the level-streaming sweep: its prefixes, per-slot scales and sums
+    plan.str_n = plan.cls_end[kClsGlobal] - plan.cls_begin[kClsGlobal];
+    plan.str_nslots = 0;
+    if (plan.str_n > 0) {
+        const int64_t n = plan.str_n, b0 = plan.cls_begin[kClsGlobal];
+        std::vector<int64_t> so((size_t)n + 1, 0);
+        for (int64_t j = 0; j < n; j++) so[(size_t)j + 1] = so[(size_t)j] + plan.items_h[(size_t)(b0 + j)].ns;
+        plan.str_nslots = so[(size_t)n];
+        auto own = [&](void **p, size_t bytes) -> int {
+            PASUR_TRY(dev_alloc(ctx, p, bytes));
+            owned.push_back({*p, bytes});
+            return PASUR_OK;
+        };
+        PASUR_TRY(own((void **)&plan.str_pairs, sizeof(int64_t) * 8 * (size_t)(n + 1)));
+        PASUR_TRY(own((void **)&plan.str_locs, sizeof(int64_t) * (size_t)(n + 1)));
+        PASUR_TRY(own((void **)&plan.str_slots, sizeof(int64_t) * (size_t)(n + 1)));
+        PASUR_TRY(own((void **)&plan.str_tu, sizeof(uint32_t) * (size_t)plan.str_nslots));
+        PASUR_TRY(own((void **)&plan.str_acc, sizeof(double) * (size_t)plan.str_nslots));
+        PASUR_CUDA(ctx, cudaMemcpyAsync(plan.str_slots, so.data(), sizeof(int64_t) * so.size(), cudaMemcpyHostToDevice,
+                                        ctx->stream));
+        k_stream_plan<<<1, 32, 0, ctx->stream>>>(plan.items_d + b0, n, plan.views_d, plan.str_pairs, plan.str_locs);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
     if (!ctx->cfr_smem_raised) {
         // the attribute is global per kernel: raise it once to the largest dynamic size any plan
@@ -1533,6 +1729,35 @@ int ensure_aux(pasur_ctx *ctx) {
     return PASUR_OK;
 }
 
+// All iterations of the plan's class-5 items on stream st: set-up, 15 level launches per
+// iteration, the root sums into the running utilities.
+int stream_sweep(pasur_ctx *ctx, const CfrPlan &plan, CfrParams p, const pasur_config *cfg, cudaStream_t st) {
+    p.items = plan.items_d + plan.cls_begin[kClsGlobal];
+    StreamPlan sp{plan.str_pairs, plan.str_locs, plan.str_slots, plan.str_tu, plan.str_acc, plan.str_n};
+    const unsigned grid = (unsigned)ctx->num_sms * 8;
+    PASUR_CUDA(ctx, cudaMemsetAsync(plan.str_tu, 0, sizeof(uint32_t) * (size_t)plan.str_nslots, st));
+    k_stream_setup<<<grid, 256, 0, st>>>(p, sp);
+    ctx->launches++;
+    PASUR_CUDA(ctx, cudaGetLastError());
+    for (int il = 0; il < cfg->iters; il++)
+        for (int i = 0; i < 15; i++) {
+            const int k = i < 7 ? i : 14 - i;
+            if (cfg->variant == 1) {
+                if (i < 7) k_stream_level<1, true><<<grid, 256, 0, st>>>(p, sp, k, il);
+                else k_stream_level<1, false><<<grid, 256, 0, st>>>(p, sp, k, il);
+            } else {
+                if (i < 7) k_stream_level<0, true><<<grid, 256, 0, st>>>(p, sp, k, il);
+                else k_stream_level<0, false><<<grid, 256, 0, st>>>(p, sp, k, il);
+            }
+            ctx->launches++;
+            PASUR_CUDA(ctx, cudaGetLastError());
+        }
+    k_stream_finalize<<<grid, 256, 0, st>>>(p, sp);
+    ctx->launches++;
+    PASUR_CUDA(ctx, cudaGetLastError());
+    return PASUR_OK;
+}
+
 int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int64_t t0, const float *dcfr) {
     if (cfg->iters <= 0 || plan.n_items == 0) return PASUR_OK;
     PASUR_TRY(ensure_aux(ctx));
@@ -1553,6 +1778,13 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
         cudaStream_t st = ctx->aux[c];
         PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
         PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
+        if (c == kClsGlobal) {
+            PASUR_TRY(stream_sweep(ctx, plan, p, cfg, st));
+            PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
+            PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
+            PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
+            continue;
+        }
         p.i_begin = plan.cls_begin[c];
         p.i_end = plan.cls_end[c];
         p.counter = ctx->counter + c;

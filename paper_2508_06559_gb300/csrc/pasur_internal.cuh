@@ -234,6 +234,14 @@ struct CfrPlan {
     int64_t clu_begin[3] = {0}, clu_end[3] = {0};
     int clu_ctas[3] = {4, 8, 16};
     size_t clu_smem[3] = {0};
+    // items of class 5 (state in device memory) run as a level-streaming sweep over every SM:
+    // exclusive prefixes over those items of their (entry, slot) pairs per level [8][n + 1], of
+    // their (local node, slot) pairs [n + 1] and of their slots [n + 1]; per slot the largest
+    // |terminal value| (float bits) and the sum of the root values of the current call
+    int64_t str_n = 0, str_nslots = 0;
+    int64_t *str_pairs = nullptr, *str_locs = nullptr, *str_slots = nullptr;
+    uint32_t *str_tu = nullptr;
+    double *str_acc = nullptr;
 };
 
 struct pasur_tree {

@@ -50,7 +50,7 @@ class pasur_score(C.Structure):
 class pasur_config(C.Structure):
     _fields_ = [("variant", C.c_int32), ("iters", C.c_int32), ("rm_deadzone", C.c_float), ("dcfr_alpha", C.c_float),
                 ("dcfr_beta", C.c_float), ("dcfr_gamma", C.c_float), ("slots_per_item", C.c_int32),
-                ("threads", C.c_int32), ("split_bytes", C.c_int32)]
+                ("threads", C.c_int32), ("split_bytes", C.c_int32), ("stream_bytes", C.c_int32)]
 
 
 _lib = None
