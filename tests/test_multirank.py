@@ -68,3 +68,12 @@ def test_job_rate_sums_ranks_over_the_slowest():
     import bench
     assert bench.job_rate(3e10 + 5e10, 0.25) == pytest.approx(3.2e11)
     assert bench.reduce_over_ranks(None, 4.0, "max", "cpu") == 4.0
+
+
+def test_size_histogram_counts_per_decade():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.size_histogram([110_651, 999_999, 1_000_000, 6_474_184, 2_000_000])
+    assert h["deals"] == 5 and h["min"] == 110_651 and h["max"] == 6_474_184
+    assert h["median"] == 1_000_000
+    assert h["per_decade"] == {"1e5-1e6": 2, "1e6-1e7": 3}
