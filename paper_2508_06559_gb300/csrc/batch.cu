@@ -171,7 +171,12 @@ int build_deals(pasur_batch *b, const uint8_t *decks, std::vector<DealPlan> &dp,
         for (;;) {
             const int64_t d = next.fetch_add(1);
             if (d >= b->n_deals || failed.load()) return;
-            const int r = build_deal(b, w, decks + 52 * d, d, dp[(size_t)d]);
+            int r;
+            try {
+                r = build_deal(b, w, decks + 52 * d, d, dp[(size_t)d]);
+            } catch (...) {  // host allocation inside the build: no exception leaves the library
+                r = set_err(w, PASUR_ENOMEM, "host allocation failed");
+            }
             if (r != PASUR_OK) {
                 std::lock_guard<std::mutex> lk(mu);
                 if (err_deal < 0 || d < err_deal) err_deal = d, err_rc = r, err_msg = w->err;
@@ -182,7 +187,14 @@ int build_deals(pasur_batch *b, const uint8_t *decks, std::vector<DealPlan> &dp,
     };
     if (rc == PASUR_OK) {
         std::vector<std::thread> th;
-        for (auto &w : ws) th.emplace_back(run, w.get());
+        for (auto &w : ws) {
+            try {
+                th.emplace_back(run, w.get());
+            } catch (...) {
+                break;  // fewer threads: the shared counter hands every deal to those running
+            }
+        }
+        if (th.empty()) run(ws[0].get());
         for (auto &x : th) x.join();
     }
     // the trees (built or partly built) belong to the batch's context from here on
