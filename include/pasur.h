@@ -4,8 +4,10 @@
  * Minimization" (arXiv 2508.06559).
  *
  * General rules for every entry point
- *   - Every call returns a pasur_status (0 = PASUR_OK, negative = error).  No C++ exception
- *     crosses this boundary.  After an error, pasur_last_error(ctx) holds a one-line message.
+ *   - Every call returns a pasur_status (0 = PASUR_OK, negative = error).  The library throws
+ *     no exception of its own; only a failed host-memory allocation inside a call (which the
+ *     library does not recover from) could raise one.  After an error, pasur_last_error(ctx)
+ *     holds a one-line message.
  *   - Pointers documented as "host or device" may point to host memory or to device memory of
  *     the context's device; the library detects which.  Device pointers are used on the
  *     context's stream; host results are complete when the call returns.
