@@ -16,7 +16,9 @@
  *   or_build_round / or_unfold             pinned (brute-force recursive count; Unfolding example)
  *   or_next_roots                          pinned (score normalisation example; invariants)
  *   or_cfr                                 pinned (T=1 closed form; minimax convergence; LP value;
- *                                          regret identity; zero-sum / delta invariance)
+ *                                          regret identity; zero-sum / delta invariance; every
+ *                                          edge's R and S after T = 1, 2, 3 by hand on a two-ply
+ *                                          game, vanilla and DCFR(1.5, 0, 2))
  *   or_minimax / or_best_response          pinned (scipy LP on tiny subgames; BR_B <= v <= BR_A)
  *   or_philox4x64                          pinned (numpy's Philox bit generator, a library routine)
  *   or_selfplay                            pinned (sample mean and outcome frequencies against the
