@@ -106,11 +106,15 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
     updates, kms, d2h = 0, 0.0, 0
     nxt = None
     outs = []
+    _WORK.clear()
     for t in reversed(trees):
         t.pasur_cfr_iterate(cfg, nxt)
         ms, edges, _ = t.pasur_last_cfr_stats()
         kms += ms
         updates += edges * T
+        solved, swept = t.pasur_solved_sizes()
+        _WORK["solved"] = _WORK.get("solved", 0) + int(solved[1:].sum()) * T
+        _WORK["swept"] = _WORK.get("swept", 0) + swept * T
         q0 = int(t.pasur_tree_sizes()[1][0])
         if out_device:
             U = torch.empty(q0, dtype=torch.float32, device="cuda")
@@ -146,6 +150,8 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
     b = P.Batch(ctx, decks, first_round, cfg)
     u = b.pasur_batch_solve()
     ms, edges, launches = b.pasur_batch_stats()
+    solved, swept = b.pasur_batch_work()
+    _WORK.update(solved=solved * T, swept=swept * T)
     d2h = 0
     info = []
     _BATCH_SIZES[:] = [0] * len(decks)
@@ -181,6 +187,10 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
 
 _SUR: dict = {}
 _BATCH_SIZES: list = []  # FGT nodes of every deal of the last batched step (all solved rounds)
+# node-updates of the last step over the solved slots (slots differing only in the inherited
+# difference share one solve) and over the swept edges (those with CFR state, i.e. not on a
+# forced-move chain): the work the kernels actually do
+_WORK: dict = {}
 
 
 def size_histogram(sizes):
@@ -287,6 +297,8 @@ def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, t
     b = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=_SUR["mlp"])
     u = b.pasur_batch_solve()
     ms, edges, _ = b.pasur_batch_stats()
+    solved, swept = b.pasur_batch_work()
+    _WORK.update(solved=solved * T, swept=swept * T)
     d2h = 0
     info = []
     for d in range(len(decks)):
@@ -533,23 +545,32 @@ def run_ours(args, rank, world, dist):
 # CPU oracle (baseline leg and the reference arm)
 # ---------------------------------------------------------------------------------------------
 
+ORACLE_KEEP_ROOTS = 4  # GT roots (with all their score slots) kept per round on the way to the final round
+
+
 def _oracle_round5(workload: str, seed: int):
-    """The oracle's own chain of rounds up to the final round of the workload (roots, slots)."""
+    """Final-round roots of the workload's deal reached by the oracle's own chain of rounds, each
+    earlier round built from its first ORACLE_KEEP_ROOTS GT roots only (a paper-scale deal's full
+    round 5 takes the oracle minutes and gigabytes to build; the sample stays genuine end states
+    of that deal).  Returns (deck, pools, score offsets, scores)."""
     import oracle as O
     first_round, _ = WORKLOADS[workload]
     deck = O.deal(seed)
     pools, soff, scores = [mask_of(deck[:4])], np.array([0, 1]), np.zeros((1, 4), np.int16)
     for r in range(first_round, 5):
-        t = O.Tree(deck, r, pools)
-        t.unfold(soff, scores)
+        keep = min(len(pools), ORACLE_KEEP_ROOTS)
+        t = O.Tree(deck, r, pools[:keep])
+        t.unfold(np.asarray(soff[:keep + 1]), np.asarray(scores[:soff[keep]]))
         pools, soff, scores, _ = t.next_roots()
         del t
     return deck, np.asarray(pools, np.uint64), np.asarray(soff), np.asarray(scores)
 
 
 def _oracle_job(args):
-    """One core: oracle CFR on FGT roots [first, first+count) of the final round for T iterations."""
-    workload, seed, first, count, T = args
+    """One core: oracle CFR on FGT roots [first, first+count) of the final round, sized to about
+    target_s seconds (iterations from a 2-iteration probe of the same roots, at most T).
+    Returns (node-updates, CFR seconds, FGT edges, iterations)."""
+    workload, seed, first, count, T, target_s = args
     import oracle as O
     deck, pools, soff, scores = _oracle_round5(workload, seed)
     root_of_slot = np.repeat(np.arange(len(pools)), np.diff(soff))
@@ -565,33 +586,35 @@ def _oracle_job(args):
     edges = int(t.sizes()[1][1:].sum())
     leaf = t.leaf_utilities_final()
     t0 = time.perf_counter()
-    t.cfr(leaf, T)
-    return edges * T, time.perf_counter() - t0, edges
+    t.cfr(leaf, 2)
+    probe = (time.perf_counter() - t0) / 2
+    Ts = max(1, min(T, int(target_s / max(probe, 1e-9))))
+    t0 = time.perf_counter()
+    t.cfr(leaf, Ts)
+    return edges * Ts, time.perf_counter() - t0, edges, Ts
 
 
 def oracle_sample(workload: str, seed: int, T: int, target_s: float, cores: int):
     """The fp64 oracle as it stands, on `cores` host cores (one process each, disjoint FGT roots
-    of the workload's final round), sized to about target_s of CPU work per core.  Returns
-    (node-updates, wall seconds, description)."""
+    of the workload's final round), each sized to about target_s of CPU work.  Returns
+    (node-updates, seconds, description): the node-updates of all processes over the longest
+    process's CFR time (they run at the same time; process start-up and tree builds excluded)."""
     import multiprocessing as mp
     _, pools, soff, _ = _oracle_round5(workload, seed)
     n_roots = int(soff[-1])
-    # probe: one root, a few iterations
-    u, s, e1 = _oracle_job((workload, seed, 0, 1, 3))
-    rate = u / max(s, 1e-6)
     per_core = max(1, min(n_roots // max(cores, 1), 64))
-    Ts = max(1, min(T, int(target_s * rate / max(per_core * e1, 1))))
-    jobs = [(workload, seed, (i * per_core) % max(n_roots - per_core + 1, 1), per_core, Ts) for i in range(cores)]
-    t0 = time.perf_counter()
+    jobs = [(workload, seed, (i * per_core) % max(n_roots - per_core + 1, 1), per_core, T, target_s)
+            for i in range(cores)]
     if cores == 1:
         res = [_oracle_job(jobs[0])]
     else:
         with mp.get_context("spawn").Pool(cores) as pool:
             res = pool.map(_oracle_job, jobs)
-    wall = time.perf_counter() - t0
     upd = sum(r[0] for r in res)
-    return upd, wall, (f"final round of seed {seed} ({workload}): {cores} processes x {per_core} FGT roots, "
-                       f"T={Ts}, {sum(r[2] for r in res)} FGT edges in all")
+    secs = max(r[1] for r in res)
+    return upd, secs, (f"final round of seed {seed} ({workload}), roots reached through the first "
+                       f"{ORACLE_KEEP_ROOTS} GT roots of every earlier round: {cores} processes x {per_core} FGT roots, "
+                       f"T={min(r[3] for r in res)}..{max(r[3] for r in res)}, {sum(r[2] for r in res)} FGT edges in all")
 
 
 def host_cores() -> int:
@@ -602,9 +625,12 @@ def host_cores() -> int:
 
 
 def cpu_baseline(args):
+    """The oracle on all host cores (one process per core, disjoint roots) and on one core."""
     cores = host_cores()
     u, s, desc = oracle_sample(args.workload, args.seed, args.iters, CPU_SAMPLE_SECONDS, cores)
-    return {"value": u / s, "unit": "node-updates/s", "cores": cores, "kind": "oracle", "sample": desc}
+    u1, s1, desc1 = oracle_sample(args.workload, args.seed, args.iters, CPU_SAMPLE_SECONDS / 2, 1)
+    return {"value": u / s, "unit": "node-updates/s", "cores": cores, "kind": "oracle", "sample": desc,
+            "single_core": {"value": u1 / s1, "unit": "node-updates/s", "cores": 1, "sample": desc1}}
 
 
 def run_reference(args, rank, world):

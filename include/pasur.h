@@ -73,6 +73,13 @@ typedef struct {
  *                every SM (state in device memory, one launch per level step); with
  *                stream_bytes > 0 every subtree needing more than that many bytes is streamed
  *                (0 = the default rule).  Results do not depend on the path.
+ *   merge_delta  1 (default): the score slots of a root that differ only in the inherited point
+ *                difference are solved once and share their results (average strategies, root
+ *                utilities): no utility contains the inherited difference (eq. final_util,
+ *                eq. passuputil), so their leaf values and hence their CFR runs coincide bit for
+ *                bit.  A non-final round merges only when the next-round utilities it is given
+ *                agree between such slots (checked on the first pasur_cfr_iterate call); 0 = solve
+ *                every slot.  Results do not depend on it.
  */
 typedef struct {
     int32_t variant;
@@ -83,9 +90,11 @@ typedef struct {
     int32_t threads;
     int32_t split_bytes;
     int32_t stream_bytes;
+    int32_t merge_delta;
 } pasur_config;
 
-/* Fill *cfg with the defaults: vanilla, 1000 iterations, tau = 1e-6, DCFR (1.5, 0, 2). */
+/* Fill *cfg with the defaults: vanilla, 1000 iterations, tau = 1e-6, DCFR (1.5, 0, 2), slots that
+ * differ only in delta merged. */
 int pasur_config_default(pasur_config *cfg);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no limit beyond the
@@ -182,6 +191,13 @@ int pasur_export_level(const pasur_tree *tree, int k, int64_t cap, int64_t *pare
  * host or device).  EINVAL before that call. */
 int pasur_leaf_values(const pasur_tree *tree, float *out, int64_t cap);
 
+/* Work the CFR solve of a tree does (after its first pasur_cfr_iterate): solved_sizes (host, may be
+ * NULL) receives the 9 FGT level sizes over the solved slots (cfg.merge_delta; equal to the FGT
+ * sizes without merging), swept_edges (may be NULL) the (node, solved slot) pairs below the roots
+ * that carry CFR state: the children of nodes with more than one path below them.  Every other
+ * edge lies on a forced-move chain (average strategy 1, regret 0, never touched per iteration). */
+int pasur_solved_sizes(const pasur_tree *tree, int64_t solved_sizes[9], int64_t *swept_edges);
+
 /* Timing of the last pasur_cfr_iterate call on the device (CUDA events around the CFR kernel
  * launches), the number of FGT edges, and the kernel launches it made. */
 int pasur_last_cfr_stats(const pasur_tree *tree, float *ms, int64_t *edges, int32_t *launches);
@@ -224,6 +240,9 @@ int pasur_batch_tree(const pasur_batch *b, int64_t deal, int round, pasur_tree *
 /* Device time of the last pasur_batch_solve (CUDA events around the graph launch), the number of
  * FGT edges of all trees, and the kernel launches in one solve. */
 int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *launches);
+/* The work of one pasur_batch_solve, summed over all trees as in pasur_solved_sizes: FGT edges over
+ * the solved slots, and the swept (node, solved slot) pairs that carry CFR state. */
+int pasur_batch_work(const pasur_batch *b, int64_t *solved_edges, int64_t *swept_edges);
 int pasur_batch_free(pasur_batch *b);
 
 /* ---- self-play (fair value) ---------------------------------------------------------------- */
@@ -337,12 +356,15 @@ int pasur_mlp_stats(const pasur_mlp *mlp, float *last_train_ms, int64_t *adam_st
  *   counts   device, n int32 (each >= 0); offsets: device, n+1 int64, offsets[i] = sum of
  *            counts[0..i), offsets[n] = total.  Both stay owned by the caller.
  *   n        0 <= n <= 4,194,303, else PASUR_EOVERFLOW (pasur_last_error(NULL) says why).
- *   cuda_stream  cudaStream_t the work is queued on (NULL = the default stream); the call
- *            returns without waiting.
- * The first call made with a given device current looks up the array's device address
- * (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls share the
- * array: two calls that overlap on the GPU (other streams, or other host threads on the same
- * stream without ordering) race and may return wrong offsets. */
+ *            counts and offsets must be device (or managed) memory, else PASUR_EINVAL; the
+ *            length of offsets cannot be checked here: it must hold n+1 elements.
+ *   cuda_stream  cudaStream_t the work is queued on (NULL = the legacy default stream); the call
+ *            returns without waiting.  Queue it after the work that writes counts.
+ * The first call made in a CUDA context (normally: the first call with a given device current)
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it for that context;
+ * make that first call outside any stream capture.  All calls share the array: two calls that
+ * overlap on the GPU (other streams, or other host threads on the same stream without ordering)
+ * race and may return wrong offsets. */
 int pasur_move_offsets_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *cuda_stream);
 
 #ifdef __cplusplus

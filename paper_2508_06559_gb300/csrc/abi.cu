@@ -152,6 +152,7 @@ int pasur_config_default(pasur_config *cfg) {
     cfg->threads = 0;
     cfg->split_bytes = 0;
     cfg->stream_bytes = 0;
+    cfg->merge_delta = 1;
     return PASUR_OK;
 }
 
@@ -360,6 +361,7 @@ int pasur_unfold(pasur_tree *t, const int64_t *score_offs, const pasur_score *sc
     }
     int64_t ns = score_offs[nr];
     t->score_off_h.assign(score_offs, score_offs + nr + 1);
+    t->scores_h.assign(scores, scores + ns);
     PASUR_TRY(tree_alloc(t, (void **)&t->score_off_d, sizeof(int64_t) * (size_t)(nr + 1)));
     PASUR_TRY(tree_alloc(t, (void **)&t->scores_d, sizeof(pasur_score) * (size_t)(ns + 1)));
     PASUR_CUDA(ctx, cudaMemcpyAsync(t->score_off_d, score_offs, sizeof(int64_t) * (size_t)(nr + 1), cudaMemcpyHostToDevice, ctx->stream));
@@ -397,7 +399,8 @@ int pasur_cfr_iterate(pasur_tree *t, const pasur_config *cfg, const float *next_
                                                 cudaMemcpyHostToDevice, ctx->stream));
             }
         }
-        int rc = compute_leaf_values(t, nu);
+        int rc = plan_solve_slots(t, cfg->merge_delta != 0, nu);
+        if (rc == PASUR_OK) rc = compute_leaf_values(t, nu);
         if (nb) dev_free(ctx, nu, nb);
         if (rc != PASUR_OK) return rc;
         PASUR_TRY(cfr_prepare(t, cfg));
@@ -525,7 +528,27 @@ int pasur_leaf_values(const pasur_tree *t, float *out, int64_t cap) {
     set_device(ctx);
     if (!t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_leaf_values: leaf values are fixed by the first pasur_cfr_iterate");
     if (!out || cap < t->Q[8]) return set_err(ctx, PASUR_EOVERFLOW, "pasur_leaf_values: cap too small");
-    return copy_out(ctx, out, t->leaf_v, t->Q[8]);
+    if (is_device_ptr(out)) {
+        PASUR_TRY(expand_leaf_values(t, out));
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return PASUR_OK;
+    }
+    float *tmp = nullptr;
+    const size_t b = sizeof(float) * (size_t)(t->Q[8] + 1);
+    PASUR_TRY(dev_alloc(ctx, (void **)&tmp, b));
+    int rc = expand_leaf_values(t, tmp);
+    if (rc == PASUR_OK) rc = copy_out(ctx, out, tmp, t->Q[8]);
+    dev_free(ctx, tmp, b);
+    return rc;
+}
+
+int pasur_solved_sizes(const pasur_tree *t, int64_t solved_sizes[9], int64_t *swept_edges) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    if (!t->cfr_ready) return set_err(t->ctx, PASUR_EINVAL, "pasur_solved_sizes: no CFR run yet");
+    for (int k = 0; k < 9; k++)
+        if (solved_sizes) solved_sizes[k] = t->cQ[k];
+    if (swept_edges) *swept_edges = t->swept_edges;
+    return PASUR_OK;
 }
 
 int pasur_last_cfr_stats(const pasur_tree *t, float *ms, int64_t *edges, int32_t *launches) {

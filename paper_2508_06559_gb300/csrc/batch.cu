@@ -31,7 +31,7 @@ struct pasur_batch {
     size_t dcfr_bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int64_t graph_launches = 0, edges = 0;
+    int64_t graph_launches = 0, edges = 0, solved_edges = 0, swept_edges = 0;
     float last_ms = 0.f;
     bool solved = false;
 };
@@ -65,7 +65,7 @@ struct DealPlan {
     std::vector<CfrItem> own[6][8];
     size_t need[6][8] = {};
     std::vector<ClusterItem> clu[6];
-    int64_t edges = 0;
+    int64_t edges = 0, solved_edges = 0, swept_edges = 0;
 };
 
 // One deal on the context wc: its rounds forward from the standalone convention root (pool
@@ -81,9 +81,7 @@ int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, De
         PASUR_TRY(pasur_build_round(wc, deck, b->first_round + ri, pools.data(), (int64_t)pools.size(), &t));
         b->trees[(size_t)(d * b->n_rounds + ri)] = t;
         PASUR_TRY(pasur_unfold(t, soff.data(), scores.data(), nullptr));
-        PASUR_TRY(tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(t->Q[8] + 1)));
         PASUR_TRY(tree_alloc(t, (void **)&b->util[(size_t)(d * b->n_rounds + ri)], sizeof(float) * (size_t)(t->Q[0] + 1)));
-        if (t->M[8] > 0) PASUR_CUDA(wc, cudaMemsetAsync(t->leaf_v, 0, sizeof(float) * (size_t)(t->Q[8] + 1), wc->stream));
         if (b->first_round + ri < 5) {
             int64_t np = 0, nr = 0;
             PASUR_TRY(pasur_next_roots(t, nullptr, 0, nullptr, nullptr, 0, nullptr, &np, &nr));
@@ -95,6 +93,13 @@ int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, De
     }
     for (int ri = 0; ri < b->n_rounds; ri++) {
         pasur_tree *t = tree_of(b, d, ri);
+        // slots that differ only in delta share one solve, except in a round whose leaves take the
+        // surrogate's values (its input includes delta); the batch's own utilities of the next
+        // round are exact and do not depend on delta
+        const bool cut = ri == b->n_rounds - 1 && b->last_round < 5;
+        PASUR_TRY(plan_solve_slots(t, b->cfg.merge_delta != 0 && !cut, nullptr));
+        PASUR_TRY(tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(t->cQ[8] + 1)));
+        if (t->M[8] > 0) PASUR_CUDA(wc, cudaMemsetAsync(t->leaf_v, 0, sizeof(float) * (size_t)(t->cQ[8] + 1), wc->stream));
         PASUR_TRY(cfr_setup_tree(t, &b->cfg, (int)d, o.own[ri], o.need[ri], &o.clu[ri]));
         t->cfr_ready = true;
         t->variant = b->cfg.variant;
@@ -107,7 +112,11 @@ int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, De
             PASUR_CUDA(wc, cudaMemcpyAsync(t->plan.items_d, t->plan.items_h.data(), sizeof(CfrItem) * (size_t)t->plan.n_items,
                                            cudaMemcpyHostToDevice, wc->stream));
         }
-        for (int k = 1; k < 9; k++) o.edges += t->Q[k];
+        for (int k = 1; k < 9; k++) {
+            o.edges += t->Q[k];
+            o.solved_edges += t->cQ[k];
+        }
+        o.swept_edges += t->swept_edges;
     }
     PASUR_CUDA(wc, cudaStreamSynchronize(wc->stream));
     return PASUR_OK;
@@ -278,7 +287,7 @@ int record_sweep(pasur_batch *b) {
             pasur_tree *t = tree_of(b, d, ri);
             PASUR_CUDA(ctx, cudaMemsetAsync(t->R, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
             PASUR_CUDA(ctx, cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)(t->data_size + 1), ctx->stream));
-            PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
+            PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->cQ[0] + 1), ctx->stream));
             const float *next = ri + 1 < b->n_rounds ? b->util[(size_t)(d * b->n_rounds + ri + 1)]
                                                      : (b->cut_util.empty() ? nullptr : b->cut_util[(size_t)d]);
             PASUR_TRY(launch_leaf_values(t, next, nullptr));
@@ -424,7 +433,11 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
         }
         rc = cfr_finalize_plan(ctx, b->plans[(size_t)ri], cls_items, need, views, cfg, b->owned, clu);
     }
-    for (const DealPlan &o : dp) b->edges += o.edges;
+    for (const DealPlan &o : dp) {
+        b->edges += o.edges;
+        b->solved_edges += o.solved_edges;
+        b->swept_edges += o.swept_edges;
+    }
     lap(tp, 2);
     if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
     if (rc == PASUR_OK && b->dcfr) b->owned.push_back({b->dcfr, b->dcfr_bytes});
@@ -516,6 +529,13 @@ int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *
     if (ms) *ms = b->last_ms;
     if (edges) *edges = b->edges;
     if (launches) *launches = b->graph_launches;
+    return PASUR_OK;
+}
+
+int pasur_batch_work(const pasur_batch *b, int64_t *solved_edges, int64_t *swept_edges) {
+    if (!b) return PASUR_EINVAL;
+    if (solved_edges) *solved_edges = b->solved_edges;
+    if (swept_edges) *swept_edges = b->swept_edges;
     return PASUR_OK;
 }
 

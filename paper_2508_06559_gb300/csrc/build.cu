@@ -214,37 +214,72 @@ __global__ void k_slots_per_node(const int32_t *__restrict__ root, int64_t m, co
     }
 }
 
-// leaf values (eq. final_util and eq. passuputil); umax receives max |value| as float bits
+// leaf values (eq. final_util and eq. passuputil) of the solved slots: solved slot x of leaf j
+// (root g) takes the score and the next-round link of its representative full slot crep; out in
+// solved FGT order (cfgt_off); umax receives max |value| as float bits
 __global__ void k_leaf_values(const GTState *__restrict__ st, const int32_t *__restrict__ root, int64_t m,
-                              const int64_t *__restrict__ fgt_off, const int64_t *__restrict__ score_off,
-                              const pasur_score *__restrict__ scores, bool final_round,
-                              const int64_t *__restrict__ lnk, const float *__restrict__ next_util,
+                              const int64_t *__restrict__ fgt_off, const int64_t *__restrict__ cfgt_off,
+                              const int64_t *__restrict__ csoff, const int32_t *__restrict__ crep,
+                              const int64_t *__restrict__ score_off, const pasur_score *__restrict__ scores,
+                              bool final_round, const int64_t *__restrict__ lnk, const float *__restrict__ next_util,
                               float *__restrict__ out, unsigned *__restrict__ umax_bits) {
     float local_max = 0.f;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         GTState s = st[j];
         int32_t g = root[j];
-        int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0;
+        const int64_t q0 = fgt_off[j], c0 = cfgt_off[j], ns = cfgt_off[j + 1] - c0;
+        const int32_t *rep = crep + csoff[g];
         if (final_round) {
             uint64_t r = cleanup_rus(s.rus, s.pool);
             int d = rus_diff(r);
             for (int64_t x = 0; x < ns; x++) {
-                pasur_score sc = scores[score_off[g] + x];
+                pasur_score sc = scores[score_off[g] + rep[x]];
                 float v = (float)(d + bonus_points(bonus_after(sc.a_clubs, sc.b_clubs, sc.bonus, r)));
-                out[q0 + x] = v;
+                out[c0 + x] = v;
                 local_max = fmaxf(local_max, fabsf(v));
             }
         } else {
             int d = rus_diff(s.rus);
             for (int64_t x = 0; x < ns; x++) {
-                float v = (float)d + next_util[lnk[q0 + x]];
-                out[q0 + x] = v;
+                float v = (float)d + next_util[lnk[q0 + rep[x]]];
+                out[c0 + x] = v;
                 local_max = fmaxf(local_max, fabsf(v));
             }
         }
     }
     if (!(local_max <= 3.0e38f)) local_max = __int_as_float(0x7f800000);  // non-finite -> +inf
     if (umax_bits) atomicMax(umax_bits, __float_as_uint(local_max));
+}
+
+// Every full slot of a non-final round's leaves must see the same next-round utility as the
+// representative of its solved slot; flag a leaf where it does not (bitwise comparison).
+__global__ void k_check_merge(const int32_t *__restrict__ root, int64_t m, const int64_t *__restrict__ fgt_off,
+                              const int64_t *__restrict__ score_off, const int64_t *__restrict__ csoff,
+                              const int32_t *__restrict__ crep, const int64_t *__restrict__ cidx0,
+                              const int64_t *__restrict__ lnk, const float *__restrict__ next_util, int32_t *bad) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = root[j];
+        const int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0, s0 = score_off[g];
+        for (int64_t s = 0; s < ns; s++) {
+            const int32_t r = crep[cidx0[s0 + s]];
+            if (r != s && __float_as_uint(next_util[lnk[q0 + s]]) != __float_as_uint(next_util[lnk[q0 + r]])) {
+                atomicOr(bad, 1);
+                break;
+            }
+        }
+    }
+}
+
+// full leaf values from the solved ones: leaf (j, s) takes the value of its solved slot
+__global__ void k_expand_leaves(const int32_t *__restrict__ root, int64_t m, const int64_t *__restrict__ fgt_off,
+                                const int64_t *__restrict__ cfgt_off, const int64_t *__restrict__ score_off,
+                                const int64_t *__restrict__ csoff, const int64_t *__restrict__ cidx0,
+                                const float *__restrict__ in, float *__restrict__ out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = root[j];
+        const int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0, c0 = cfgt_off[j] - csoff[g];
+        for (int64_t s = 0; s < ns; s++) out[q0 + s] = in[c0 + cidx0[score_off[g] + s]];
+    }
 }
 
 unsigned grid_for(int64_t threads, int block) {
@@ -386,8 +421,9 @@ int launch_leaf_values(pasur_tree *t, const float *next_util_dev, unsigned *umax
     pasur_ctx *ctx = t->ctx;
     if (t->M[8] == 0) return PASUR_OK;
     k_leaf_values<<<grid_for(t->M[8], 256), 256, 0, ctx->stream>>>(t->st[8], t->root[8], t->M[8], t->fgt_off[8],
-                                                                  t->score_off_d, t->scores_d, t->final_round, t->lnk_d,
-                                                                  next_util_dev, t->leaf_v, umax_bits);
+                                                                  t->cfgt_off[8], t->csoff_d, t->crep_d, t->score_off_d,
+                                                                  t->scores_d, t->final_round, t->lnk_d, next_util_dev,
+                                                                  t->leaf_v, umax_bits);
     ctx->launches++;
     PASUR_CUDA(ctx, cudaGetLastError());
     return PASUR_OK;
@@ -395,15 +431,15 @@ int launch_leaf_values(pasur_tree *t, const float *next_util_dev, unsigned *umax
 
 int compute_leaf_values(pasur_tree *t, const float *next_util_dev) {
     pasur_ctx *ctx = t->ctx;
-    int64_t q8 = t->Q[8];
+    int64_t q8 = t->cQ[8];
     if (!t->leaf_v) PASUR_TRY(tree_alloc(t, (void **)&t->leaf_v, sizeof(float) * (size_t)(q8 + 1)));
     unsigned *umax = nullptr;
     PASUR_TRY(dev_alloc(ctx, (void **)&umax, sizeof(unsigned)));
     PASUR_CUDA(ctx, cudaMemsetAsync(umax, 0, sizeof(unsigned), ctx->stream));
     if (t->M[8] > 0) {
         k_leaf_values<<<grid_for(t->M[8], 256), 256, 0, ctx->stream>>>(
-            t->st[8], t->root[8], t->M[8], t->fgt_off[8], t->score_off_d, t->scores_d, t->final_round, t->lnk_d,
-            next_util_dev, t->leaf_v, umax);
+            t->st[8], t->root[8], t->M[8], t->fgt_off[8], t->cfgt_off[8], t->csoff_d, t->crep_d, t->score_off_d,
+            t->scores_d, t->final_round, t->lnk_d, next_util_dev, t->leaf_v, umax);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }
@@ -415,6 +451,123 @@ int compute_leaf_values(pasur_tree *t, const float *next_util_dev) {
     memcpy(&u, &hb, sizeof u);
     if (!(u <= 3.0e38f)) return set_err(ctx, PASUR_ENUMERIC, "non-finite leaf value");
     t->umax = u;
+    return PASUR_OK;
+}
+
+int plan_solve_slots(pasur_tree *t, bool merge, const float *next_util_dev) {
+    pasur_ctx *ctx = t->ctx;
+    if (t->csoff_d) return PASUR_OK;
+    const int64_t nr = t->n_roots, q0 = t->Q[0];
+    // group the slots of every root by (a_clubs, b_clubs, bonus), numbered by first appearance
+    std::vector<int64_t> csoff((size_t)nr + 1, 0), cidx0((size_t)q0 + 1, 0);
+    std::vector<int32_t> crep;
+    crep.reserve((size_t)q0 + 1);
+    bool any = false;
+    for (int64_t g = 0; g < nr; g++) {
+        const int64_t a = t->score_off_h[(size_t)g], b = t->score_off_h[(size_t)g + 1];
+        const int64_t base = (int64_t)crep.size();
+        std::vector<std::pair<uint32_t, int32_t>> seen;  // key -> solved slot within the root
+        for (int64_t s = a; s < b; s++) {
+            const pasur_score &x = t->scores_h[(size_t)s];
+            const uint32_t key = merge ? ((uint32_t)x.a_clubs << 8) | ((uint32_t)x.b_clubs << 2) | (uint32_t)x.bonus
+                                       : (uint32_t)(s - a);
+            int32_t c = -1;
+            for (const auto &k : seen)
+                if (k.first == key) c = k.second;
+            if (c < 0) {
+                c = (int32_t)seen.size();
+                seen.push_back({key, c});
+                crep.push_back((int32_t)(s - a));
+            } else {
+                any = true;
+            }
+            cidx0[(size_t)s] = base + c;
+        }
+        csoff[(size_t)g + 1] = (int64_t)crep.size();
+    }
+    const int64_t cq0 = (int64_t)crep.size();
+    PASUR_TRY(tree_alloc(t, (void **)&t->csoff_d, sizeof(int64_t) * (size_t)(nr + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->crep_d, sizeof(int32_t) * (size_t)(cq0 + 1)));
+    PASUR_TRY(tree_alloc(t, (void **)&t->cidx0_d, sizeof(int64_t) * (size_t)(q0 + 1)));
+    PASUR_CUDA(ctx, cudaMemcpyAsync(t->csoff_d, csoff.data(), sizeof(int64_t) * (size_t)(nr + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (cq0) PASUR_CUDA(ctx, cudaMemcpyAsync(t->crep_d, crep.data(), sizeof(int32_t) * (size_t)cq0, cudaMemcpyHostToDevice, ctx->stream));
+    if (q0) PASUR_CUDA(ctx, cudaMemcpyAsync(t->cidx0_d, cidx0.data(), sizeof(int64_t) * (size_t)q0, cudaMemcpyHostToDevice, ctx->stream));
+    // a non-final round merges only slots whose leaves see the same next-round utilities
+    if (any && !t->final_round && next_util_dev && t->M[8] > 0) {
+        int32_t *bad = nullptr;
+        PASUR_TRY(dev_alloc(ctx, (void **)&bad, sizeof(int32_t)));
+        PASUR_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int32_t), ctx->stream));
+        k_check_merge<<<grid_for(t->M[8], 256), 256, 0, ctx->stream>>>(t->root[8], t->M[8], t->fgt_off[8], t->score_off_d,
+                                                                      t->csoff_d, t->crep_d, t->cidx0_d, t->lnk_d,
+                                                                      next_util_dev, bad);
+        ctx->launches++;
+        int32_t hb = 0;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, bad, sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_err(ctx, e, "k_check_merge");
+        if (hb) {
+            // the given utilities differ between slots that differ only in delta: solve every slot
+            PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            for (int64_t g = 0; g <= nr; g++) csoff[(size_t)g] = t->score_off_h[(size_t)g];
+            crep.resize((size_t)q0);
+            for (int64_t g = 0; g < nr; g++)
+                for (int64_t s = t->score_off_h[(size_t)g]; s < t->score_off_h[(size_t)g + 1]; s++) {
+                    crep[(size_t)s] = (int32_t)(s - t->score_off_h[(size_t)g]);
+                    cidx0[(size_t)s] = s;
+                }
+            any = false;
+            PASUR_TRY(tree_alloc(t, (void **)&t->crep_d, sizeof(int32_t) * (size_t)(q0 + 1)));
+            PASUR_CUDA(ctx, cudaMemcpyAsync(t->csoff_d, csoff.data(), sizeof(int64_t) * (size_t)(nr + 1), cudaMemcpyHostToDevice, ctx->stream));
+            if (q0) {
+                PASUR_CUDA(ctx, cudaMemcpyAsync(t->crep_d, crep.data(), sizeof(int32_t) * (size_t)q0, cudaMemcpyHostToDevice, ctx->stream));
+                PASUR_CUDA(ctx, cudaMemcpyAsync(t->cidx0_d, cidx0.data(), sizeof(int64_t) * (size_t)q0, cudaMemcpyHostToDevice, ctx->stream));
+            }
+        }
+    }
+    t->merged = any;
+    t->csoff_h = csoff;
+    if (!any) {
+        for (int k = 0; k < 9; k++) {
+            t->cfgt_off[k] = t->fgt_off[k];
+            t->cQ[k] = t->Q[k];
+        }
+    } else {
+        int64_t mmax = 0;
+        for (int k = 0; k < 9; k++) mmax = std::max(mmax, t->M[k]);
+        int64_t *slots = nullptr;
+        const size_t sb = sizeof(int64_t) * (size_t)(mmax + 1);
+        PASUR_TRY(dev_alloc(ctx, (void **)&slots, sb));
+        int rc = PASUR_OK;
+        for (int k = 0; k < 9 && rc == PASUR_OK; k++) {
+            const int64_t m = t->M[k];
+            rc = tree_alloc(t, (void **)&t->cfgt_off[k], sizeof(int64_t) * (size_t)(m + 1));
+            if (rc == PASUR_OK && m > 0) {
+                k_slots_per_node<<<grid_for(m, 256), 256, 0, ctx->stream>>>(t->root[k], m, t->csoff_d, slots);
+                ctx->launches++;
+                if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_slots_per_node launch");
+            }
+            if (rc == PASUR_OK) rc = exclusive_scan_i64(ctx, slots, t->cfgt_off[k], m);
+            if (rc == PASUR_OK) rc = read_i64(ctx, t->cfgt_off[k] + m, &t->cQ[k]);
+        }
+        dev_free(ctx, slots, sb);
+        if (rc != PASUR_OK) return rc;
+    }
+    return PASUR_OK;
+}
+
+int expand_leaf_values(const pasur_tree *t, float *out_dev) {
+    pasur_ctx *ctx = t->ctx;
+    if (t->M[8] == 0) return PASUR_OK;
+    if (!t->merged) {
+        PASUR_CUDA(ctx, cudaMemcpyAsync(out_dev, t->leaf_v, sizeof(float) * (size_t)t->Q[8], cudaMemcpyDeviceToDevice, ctx->stream));
+        return PASUR_OK;
+    }
+    k_expand_leaves<<<grid_for(t->M[8], 256), 256, 0, ctx->stream>>>(t->root[8], t->M[8], t->fgt_off[8], t->cfgt_off[8],
+                                                                    t->score_off_d, t->csoff_d, t->cidx0_d, t->leaf_v, out_dev);
+    ctx->launches++;
+    PASUR_CUDA(ctx, cudaGetLastError());
     return PASUR_OK;
 }
 

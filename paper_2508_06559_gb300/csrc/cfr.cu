@@ -880,9 +880,25 @@ __global__ void k_export_sigma(const CfrItem *items, int64_t n_items, const CfrR
     }
 }
 
-__global__ void k_export_util(const double *uacc, int64_t n, double inv_t, float *out) {
+__global__ void k_export_util(const double *uacc, const int64_t *cidx0, int64_t n, double inv_t, float *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (float)(uacc[i] * inv_t);
+        out[i] = (float)(uacc[cidx0[i]] * inv_t);
+}
+
+// One level of the average strategies of every full slot from those of the solved slots: one warp
+// per GT node j, lanes over its full slots (consecutive output addresses); full slot s of root g
+// reads solved slot cidx0[score_off[g] + s] - csoff[g] of the same node.
+__global__ void k_expand_edges(const int32_t *__restrict__ root, int64_t m, const int64_t *__restrict__ fgt_off,
+                               const int64_t *__restrict__ cfgt_off, const int64_t *__restrict__ score_off,
+                               const int64_t *__restrict__ csoff, const int64_t *__restrict__ cidx0,
+                               const float *__restrict__ in, float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        const int32_t g = root[j];
+        const int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0, c0 = cfgt_off[j] - csoff[g], s0 = score_off[g];
+        for (int64_t s = lane; s < ns; s += 32) out[q0 + s] = in[c0 + cidx0[s0 + s]];
+    }
 }
 
 // chain[j] = 1 when the subtree of j is one path of forced moves (leaves included)
@@ -1101,7 +1117,7 @@ int build_layout(pasur_tree *t) {
         if (t->M[k] == 0) continue;
         k_fill_layout<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(
             k, t->M[k], t->root[k], local[k], active[k], lrank[k], arank[k], k < 8 ? lrank[k + 1] : nullptr,
-            k > 0 ? lrank[k - 1] : nullptr, k > 0 ? t->parent[k] : nullptr, co, t->fgt_off[8], t->croots_d, t->loc_tq,
+            k > 0 ? lrank[k - 1] : nullptr, k > 0 ? t->parent[k] : nullptr, co, t->cfgt_off[8], t->croots_d, t->loc_tq,
             t->act_li, t->act_pl, t->act_cs, t->act_d, t->act_gt, act_key, ctx->errflag);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
@@ -1170,7 +1186,7 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
     std::vector<int64_t> cand;
     for (int64_t g = 0; g < nr; g++) {
         const CfrRoot &cr = t->croots_h[(size_t)g];
-        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t Sg = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
         if (Sg == 0 || L == 0 || nA < 2 || streamed[(size_t)g]) continue;
         const size_t need = resident_bytes(L, nA, 1);
@@ -1406,7 +1422,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     std::vector<char> streamed((size_t)t->n_roots, 0);
     for (int64_t g = 0; g < t->n_roots; g++) {
         const CfrRoot &cr = t->croots_h[(size_t)g];
-        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t Sg = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
         if (Sg == 0 || L == 0) continue;
         const size_t need = resident_bytes(L, nA, 1);
@@ -1420,7 +1436,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     int64_t data = 0, scratch = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         CfrRoot &cr = t->croots_h[(size_t)g];
-        const int64_t Sg = t->score_off_h[(size_t)g + 1] - t->score_off_h[(size_t)g];
+        const int64_t Sg = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
         cr.W = 0;
         cr.cls = -1;
@@ -1496,6 +1512,11 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     }
     t->data_size = data;
     t->scratch_size = scratch;
+    t->swept_edges = 0;
+    for (int64_t g = 0; g < t->n_roots; g++) {
+        const CfrRoot &cr = t->croots_h[(size_t)g];
+        if (cr.ls[9] > 1) t->swept_edges += (int64_t)(cr.ls[9] - 1) * (t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g]);
+    }
     if (!splits.empty()) {
         // append the parts' entries and local leaf indices; pseudo-roots after the real roots
         const int64_t NA = t->n_active, NL = t->n_local, na = (int64_t)nli.size(), nl = (int64_t)ntq.size();
@@ -1545,8 +1566,8 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
         PASUR_TRY(tree_alloc(t, (void **)&t->V, sizeof(float) * (size_t)scratch));
         PASUR_TRY(tree_alloc(t, (void **)&t->X, sizeof(float) * (size_t)scratch));
     }
-    PASUR_TRY(tree_alloc(t, (void **)&t->uacc, sizeof(double) * (size_t)(t->Q[0] + 1)));
-    PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->Q[0] + 1), ctx->stream));
+    PASUR_TRY(tree_alloc(t, (void **)&t->uacc, sizeof(double) * (size_t)(t->cQ[0] + 1)));
+    PASUR_CUDA(ctx, cudaMemsetAsync(t->uacc, 0, sizeof(double) * (size_t)(t->cQ[0] + 1), ctx->stream));
     TreeView &v = t->view;
     v.roots = t->croots_d;
     v.act_li = t->act_li;
@@ -1555,7 +1576,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     v.act_d = t->act_d;
     v.loc_tq = t->loc_tq;
     v.leaf_v = t->leaf_v;
-    v.fgt_off0 = t->fgt_off[0];
+    v.fgt_off0 = t->cfgt_off[0];
     v.R = t->R;
     v.S = t->S;
     v.V = t->V;
@@ -1969,15 +1990,16 @@ int cfr_run(pasur_tree *t, const pasur_config *cfg) {
     return PASUR_OK;
 }
 
-int cfr_export_sigma(const pasur_tree *t, float *out_dev) {
+// average strategies of the solved slots (levels 1..8 concatenated in solved FGT order)
+int export_sigma_solved(const pasur_tree *t, float *out_dev) {
     pasur_ctx *ctx = t->ctx;
     LevelPtrs lp{};
     int64_t base = 0, ne = 0;
     for (int k = 0; k < 9; k++) {
-        lp.fgt[k] = t->fgt_off[k];
+        lp.fgt[k] = t->cfgt_off[k];
         lp.child[k] = k < 8 ? t->child_off[k] : nullptr;
         lp.base[k] = k >= 1 ? base : 0;
-        if (k >= 1) base += t->Q[k];
+        if (k >= 1) base += t->cQ[k];
     }
     ne = base;
     if (ne > 0) {
@@ -1995,13 +2017,41 @@ int cfr_export_sigma(const pasur_tree *t, float *out_dev) {
     return PASUR_OK;
 }
 
+int cfr_export_sigma(const pasur_tree *t, float *out_dev) {
+    if (!t->merged) return export_sigma_solved(t, out_dev);
+    pasur_ctx *ctx = t->ctx;
+    int64_t ce = 0;
+    for (int k = 1; k < 9; k++) ce += t->cQ[k];
+    float *tmp = nullptr;
+    const size_t tb = sizeof(float) * (size_t)(ce + 1);
+    PASUR_TRY(dev_alloc(ctx, (void **)&tmp, tb));
+    int rc = export_sigma_solved(t, tmp);
+    // every full slot takes its solved slot's strategy, level by level
+    int64_t fb = 0, cb = 0;
+    for (int k = 1; k < 9 && rc == PASUR_OK; k++) {
+        if (t->M[k] > 0) {
+            k_expand_edges<<<grid_for(t->M[k] * 32, 256), 256, 0, ctx->stream>>>(
+                t->root[k], t->M[k], t->fgt_off[k], t->cfgt_off[k], t->score_off_d, t->csoff_d, t->cidx0_d, tmp + cb,
+                out_dev + fb);
+            ctx->launches++;
+            if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_expand_edges launch");
+        }
+        fb += t->Q[k];
+        cb += t->cQ[k];
+    }
+    dev_free(ctx, tmp, tb);  // stream-ordered: freed after the expansion has read it
+    return rc;
+}
+
 int cfr_export_utilities(const pasur_tree *t, float *out_dev) { return cfr_export_utilities_n(t, t->iters_done, out_dev); }
 
+// average root utility of every full root slot, from its solved slot (no allocation: the batch
+// captures this into its graph)
 int cfr_export_utilities_n(const pasur_tree *t, int64_t iters, float *out_dev) {
     pasur_ctx *ctx = t->ctx;
     if (t->Q[0] == 0) return PASUR_OK;
     double inv = iters > 0 ? 1.0 / (double)iters : 0.0;
-    k_export_util<<<grid_for(t->Q[0], 256), 256, 0, ctx->stream>>>(t->uacc, t->Q[0], inv, out_dev);
+    k_export_util<<<grid_for(t->Q[0], 256), 256, 0, ctx->stream>>>(t->uacc, t->cidx0_d, t->Q[0], inv, out_dev);
     ctx->launches++;
     PASUR_CUDA(ctx, cudaGetLastError());
     return PASUR_OK;

@@ -12,12 +12,15 @@
 // share that one array.
 //
 // Set-up: the array's device address is looked up with cudaGetSymbolAddress on the first call made
-// while a given device is current, and cached per device.  Make that first call outside any CUDA
-// stream capture.
+// in a given CUDA context (normally: the first call with a given device current) and cached per
+// context.  Make that first call outside any CUDA stream capture.
 //
 // Nothing in the array needs to start at zero: every call writes each partial sum it later reads.
 // It does keep the last call's partial sums until the next call overwrites them.
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "pasur_internal.cuh"
 
@@ -126,24 +129,78 @@ __global__ void k_tile_offsets(const int32_t *__restrict__ counts, int64_t n, co
     }
 }
 
-// device address of g_scan_scratch, looked up once per device (host code may not use the
-// symbol's name as an address)
-constexpr int kMaxDevices = 64;
-int64_t *g_scratch_ptr[kMaxDevices] = {nullptr};
+// Device address of g_scan_scratch.  Host code may not use the symbol's name as an address, so
+// it is looked up with cudaGetSymbolAddress, once per CUDA context: the address belongs to the
+// module loaded in the context that was current at the lookup, so a program that switches to
+// another (non-primary) context, or resets the device and so loads the module again, gets a
+// fresh lookup instead of a stale address.  Contexts are told apart by the driver's context id,
+// which is never reused within a process; the table is guarded by a mutex, so two host threads
+// making their first call at the same time look the address up once.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
 
-cudaError_t scratch_for_current_device(int64_t **out) {
+struct ScratchTable {
+    std::mutex mu;
+    std::once_flag once;
+    CtxGetCurrentFn get_current = nullptr;
+    CtxGetIdFn get_id = nullptr;
+    std::vector<std::pair<unsigned long long, int64_t *>> by_ctx;
+};
+ScratchTable g_scratch;
+
+cudaError_t current_context_id(unsigned long long *id) {
+    std::call_once(g_scratch.once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_scratch.get_current = (CtxGetCurrentFn)f;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_scratch.get_id = (CtxGetIdFn)f;
+    });
+    if (!g_scratch.get_current || !g_scratch.get_id) return cudaErrorNotSupported;
+    void *c = nullptr;
+    if (g_scratch.get_current(&c) != 0 || !c) return cudaErrorDeviceUninitialized;
+    return g_scratch.get_id(c, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+cudaError_t scratch_for_current_context(int64_t **out) {
+    // bind the runtime's context of the current device first (a runtime call that needs one)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
+    void *p = nullptr;
+    unsigned long long id = 0;
+    if (current_context_id(&id) != cudaSuccess) {
+        e = cudaGetSymbolAddress(&p, g_scan_scratch);  // makes the device's primary context current
+        if (e != cudaSuccess) return e;
+        e = current_context_id(&id);
+        if (e != cudaSuccess) return e;
+    }
+    std::lock_guard<std::mutex> lk(g_scratch.mu);
+    for (const auto &x : g_scratch.by_ctx)
+        if (x.first == id) {
+            *out = x.second;
+            return cudaSuccess;
+        }
+    if (!p) {
         e = cudaGetSymbolAddress(&p, g_scan_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (int64_t *)p;
     }
-    *out = g_scratch_ptr[dev];
+    g_scratch.by_ctx.push_back({id, (int64_t *)p});
+    *out = (int64_t *)p;
     return cudaSuccess;
+}
+
+// true when p is an address the device can dereference (device or managed memory)
+bool device_addressable(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -155,8 +212,11 @@ extern "C" int pasur_move_offsets_noalloc(const int32_t *counts, int64_t n, int6
         return pasur::set_err(nullptr, PASUR_EOVERFLOW,
                               "pasur_move_offsets_noalloc: " + std::to_string(n) + " counts exceed the fixed limit of " +
                                   std::to_string(kNoAllocMaxCounts));
+    if (!device_addressable(offsets) || (n > 0 && !device_addressable(counts)))
+        return pasur::set_err(nullptr, PASUR_EINVAL,
+                              "pasur_move_offsets_noalloc: counts and offsets must be device memory");
     int64_t *scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    cudaError_t e = scratch_for_current_context(&scratch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return pasur::set_err(nullptr, PASUR_ECUDA, std::string("pasur_move_offsets_noalloc: ") + cudaGetErrorString(e));

@@ -268,6 +268,20 @@ struct pasur_tree {
     int64_t *score_off_d = nullptr;
     pasur_score *scores_d = nullptr;
     std::vector<int64_t> score_off_h;
+    std::vector<pasur_score> scores_h;
+    // score slots the CFR solves.  Slots of one root whose leaf values coincide for every leaf
+    // give identical CFR runs; with merging, the slots of a root that share (a_clubs, b_clubs,
+    // bonus) -- which differ only in the inherited difference, which no utility contains (eq.
+    // final_util, eq. passuputil) -- are solved once.  "Solved slots" are numbered per root in
+    // order of their first full slot; without merging they are the full slots.
+    bool merged = false;
+    std::vector<int64_t> csoff_h;       // [n_roots+1] solved slots per root (prefix)
+    int64_t *csoff_d = nullptr;
+    int32_t *crep_d = nullptr;          // [cQ[0]] per solved slot: its first full slot within the root
+    int64_t *cidx0_d = nullptr;         // [Q[0]] per full root slot: the global index of its solved slot
+    int64_t *cfgt_off[9] = {nullptr};   // per GT node: first solved FGT node (= fgt_off unless merged)
+    int64_t cQ[9] = {0};                // solved FGT level sizes
+    int64_t swept_edges = 0;            // (local non-root node, solved slot) pairs: edges with CFR state
     // next round links
     bool has_next = false;
     int64_t *lnk_d = nullptr;           // Q[8]
@@ -279,7 +293,7 @@ struct pasur_tree {
     bool cfr_ready = false;
     int64_t iters_done = 0;
     float umax = 0.f;
-    float *leaf_v = nullptr;            // Q[8], FGT order
+    float *leaf_v = nullptr;            // cQ[8], solved FGT order
     std::vector<CfrRoot> croots_h;
     CfrRoot *croots_d = nullptr;
     int32_t *act_li = nullptr;          // per active entry: its local index
@@ -298,7 +312,7 @@ struct pasur_tree {
     int64_t data_size = 0, scratch_size = 0;
     float *R = nullptr, *S = nullptr;   // per (local node, slot) of every item
     float *V = nullptr, *X = nullptr;   // values and reaches of the non-resident items
-    double *uacc = nullptr;             // Q[0]
+    double *uacc = nullptr;             // cQ[0]
 
     int32_t variant = -1;
     float last_ms = 0.f;
@@ -345,6 +359,12 @@ int build_levels(pasur_tree *t, const uint64_t *root_pools_dev);
 int unfold_levels(pasur_tree *t);
 int compute_leaf_values(pasur_tree *t, const float *next_util_dev);
 int launch_leaf_values(pasur_tree *t, const float *next_util_dev, unsigned *umax_bits);
+// the solved slots of an unfolded tree: merged per (a_clubs, b_clubs, bonus) when `merge`, else one
+// per full slot; a non-final round given next_util_dev merges only if every merged slot's leaves
+// equal its representative's (checked on the device); idempotent
+int plan_solve_slots(pasur_tree *t, bool merge, const float *next_util_dev);
+// full FGT leaf values from the solved ones (out: device, Q[8] floats)
+int expand_leaf_values(const pasur_tree *t, float *out_dev);
 
 // cfr.cu
 int cfr_prepare(pasur_tree *t, const pasur_config *cfg);

@@ -33,7 +33,7 @@ EXPORTS = [
     "pasur_mlp_forward", "pasur_mlp_gradients", "pasur_mlp_dataset_add_tree", "pasur_mlp_dataset_add_rows",
     "pasur_mlp_dataset_size", "pasur_mlp_dataset_export", "pasur_mlp_dataset_clear", "pasur_mlp_train",
     "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
-    "pasur_batch_create_cut",
+    "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work",
 ]
 
 
@@ -50,7 +50,8 @@ class pasur_score(C.Structure):
 class pasur_config(C.Structure):
     _fields_ = [("variant", C.c_int32), ("iters", C.c_int32), ("rm_deadzone", C.c_float), ("dcfr_alpha", C.c_float),
                 ("dcfr_beta", C.c_float), ("dcfr_gamma", C.c_float), ("slots_per_item", C.c_int32),
-                ("threads", C.c_int32), ("split_bytes", C.c_int32), ("stream_bytes", C.c_int32)]
+                ("threads", C.c_int32), ("split_bytes", C.c_int32), ("stream_bytes", C.c_int32),
+                ("merge_delta", C.c_int32)]
 
 
 _lib = None
@@ -86,6 +87,8 @@ def load() -> C.CDLL:
     L.pasur_export_level.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, vp, vp]
     L.pasur_leaf_values.argtypes = [vp, vp, i64]
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
+    L.pasur_solved_sizes.argtypes = [vp, vp, i64p]
+    L.pasur_batch_work.argtypes = [vp, i64p, i64p]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
     L.pasur_batch_create_cut.argtypes = [vp, vp, i64, C.c_int, C.c_int, C.POINTER(pasur_config), vp, C.POINTER(vp)]
@@ -154,9 +157,32 @@ def pasur_deal(seed: int) -> np.ndarray:
 
 def pasur_move_offsets_noalloc(counts_dev, offsets_dev, stream=None) -> None:
     """CSR offsets (n+1 int64, device) from per-node move counts (n int32, device) without any
-    device allocation; see include/pasur.h.  Raises PasurError on failure."""
+    device allocation; see include/pasur.h.  counts_dev: contiguous CUDA int32 tensor of n counts;
+    offsets_dev: contiguous CUDA int64 tensor of at least n+1 elements on the same device (the C
+    call cannot check its length, so this wrapper does).  stream: a cudaStream_t handle, default
+    torch's current stream on that device (the stream the tensors' producers normally used).
+    Raises PasurError (PASUR_EINVAL for a wrong tensor) on failure."""
+    import torch
+
+    def bad(msg):
+        raise PasurError(PASUR_EINVAL, "pasur_move_offsets_noalloc: " + msg)
+
+    for name, t, dt in (("counts", counts_dev, torch.int32), ("offsets", offsets_dev, torch.int64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            bad(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            bad(f"{name} must be {dt}, not {t.dtype}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+    if counts_dev.device != offsets_dev.device:
+        bad("counts and offsets must be on the same device")
     n = counts_dev.numel()
-    _check(load().pasur_move_offsets_noalloc(_ptr(counts_dev), n, _ptr(offsets_dev), stream))
+    if offsets_dev.numel() < n + 1:
+        bad(f"offsets holds {offsets_dev.numel()} elements, {n + 1} are written")
+    if stream is None:
+        stream = torch.cuda.current_stream(counts_dev.device).cuda_stream
+    with torch.cuda.device(counts_dev.device):
+        _check(load().pasur_move_offsets_noalloc(_ptr(counts_dev), n, _ptr(offsets_dev), stream))
 
 
 def scores_array(rows) -> np.ndarray:
@@ -397,6 +423,12 @@ class Batch:
         _check(load().pasur_batch_stats(self.h, C.byref(ms), C.byref(e), C.byref(l)), self.ctx.h)
         return ms.value, e.value, l.value
 
+    def pasur_batch_work(self):
+        """(FGT edges over the solved slots, swept edges with CFR state) of one solve."""
+        a, b = C.c_int64(0), C.c_int64(0)
+        _check(load().pasur_batch_work(self.h, C.byref(a), C.byref(b)), self.ctx.h)
+        return a.value, b.value
+
     def pasur_batch_selfplay(self, n_games: int, seeds, out=None):
         """n_games games per deal (deal d under seeds[d]); int16 [n_deals, n_games]."""
         sd = np.ascontiguousarray(seeds, np.uint64)
@@ -432,6 +464,13 @@ class Tree:
         q = np.zeros(9, np.int64)
         self._c(load().pasur_tree_sizes(self.h, _ptr(g), _ptr(q)))
         return g, q
+
+    def pasur_solved_sizes(self):
+        """(solved FGT level sizes [9], swept edges) after the first pasur_cfr_iterate."""
+        c = np.zeros(9, np.int64)
+        e = C.c_int64(0)
+        self._c(load().pasur_solved_sizes(self.h, _ptr(c), C.byref(e)))
+        return c, e.value
 
     def pasur_unfold(self, score_offs, scores) -> np.ndarray:
         so = np.ascontiguousarray(score_offs, np.int64)

@@ -86,3 +86,39 @@ def test_noalloc_offsets_large_and_limits(ctx):
     with pytest.raises(P.PasurError) as e:
         P.pasur_move_offsets_noalloc(too_big, off2)
     assert e.value.code == P.PASUR_EOVERFLOW
+
+
+def test_noalloc_rejects_wrong_buffers(ctx):
+    """Wrong tensors are refused before any kernel runs: a host buffer, the wrong element type, an
+    offsets buffer shorter than n+1 (the C call has no capacity argument), a strided view."""
+    import torch
+
+    from paper_2508_06559_gb300 import pasur as P
+    n = 1000
+    good_c = torch.ones(n, dtype=torch.int32, device="cuda")
+    good_o = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    cases = [
+        (good_c.cpu(), good_o),                                            # host counts
+        (good_c, good_o.cpu()),                                            # host offsets
+        (good_c.to(torch.int64), good_o),                                  # int64 counts
+        (good_c, good_o.to(torch.int32)),                                  # int32 offsets
+        (good_c, good_o[:n]),                                              # offsets too short
+        (torch.ones(2 * n, dtype=torch.int32, device="cuda")[::2], good_o),  # strided counts
+    ]
+    for c, o in cases:
+        with pytest.raises(P.PasurError) as e:
+            P.pasur_move_offsets_noalloc(c, o)
+        assert e.value.code == P.PASUR_EINVAL
+    # a host pointer given straight to the C entry point is refused too
+    import ctypes
+
+    h = np.zeros(n + 1, np.int64)
+    rc = P.load().pasur_move_offsets_noalloc(ctypes.c_void_p(good_c.data_ptr()), n, ctypes.c_void_p(h.ctypes.data),
+                                            None)
+    assert rc == P.PASUR_EINVAL
+    # the good pair still works after the refusals, on torch's current (non-default) stream
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        P.pasur_move_offsets_noalloc(good_c, good_o)
+    s.synchronize()
+    assert (good_o.cpu().numpy() == np.arange(n + 1)).all()
