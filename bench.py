@@ -47,6 +47,9 @@ METRIC = "CFR node-updates/sec"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 ALG_BYTES_PER_UPDATE = 16   # regret and strategy sum, f32, read + write, per node-update
 CPU_SAMPLE_SECONDS = 12.0
+# the first seed (counting from 0) whose complete six-round full game tree has over 1e9 nodes, the
+# paper's average deal size: 3.38e9 FGT nodes (seed 0 has 3.4e7)
+FULL_GAME_SEED = 47
 
 
 def mask_of(cards) -> int:
@@ -90,7 +93,7 @@ def selfplay_summary(ctx, games):
 
 def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
     """One step.  Returns (node_updates, cfr_kernel_ms, nontrivial_edges_x_T, bytes_h2d, bytes_d2h, trees_info)."""
-    cfg = P.pasur_config_default(iters=T)
+    cfg = P.pasur_config_default(iters=T, **SOLVER)
     trees = []
     pools = np.array([mask_of(deck[:4])], np.uint64)
     soff = np.array([0, 1], np.int64)
@@ -146,7 +149,7 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
 def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
     """One step of the batched workload: build every deal's rounds, solve them in the batch,
     write out every tree's average strategies and root utilities, free."""
-    cfg = P.pasur_config_default(iters=T)
+    cfg = P.pasur_config_default(iters=T, **SOLVER)
     b = P.Batch(ctx, decks, first_round, cfg)
     u = b.pasur_batch_solve()
     ms, edges, launches = b.pasur_batch_stats()
@@ -191,6 +194,7 @@ _BATCH_SIZES: list = []  # FGT nodes of every deal of the last batched step (all
 # difference share one solve) and over the swept edges (those with CFR state, i.e. not on a
 # forced-move chain): the work the kernels actually do
 _WORK: dict = {}
+SOLVER: dict = {}  # solver settings from the command line (pasur_config fields)
 
 
 def size_histogram(sizes):
@@ -235,7 +239,7 @@ def surrogate_setup(P, ctx, decks, T, torch):
     train_ms, steps = mlp.stats()
     none = P.Mlp(ctx)
     none.set_params(no_learning_params(P))
-    cfg = P.pasur_config_default(iters=T)
+    cfg = P.pasur_config_default(iters=T, **SOLVER)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     be = P.Batch(ctx, decks, 0, cfg)
@@ -293,7 +297,7 @@ def surrogate_setup(P, ctx, decks, T, torch):
 def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
     """One step of the surrogate workload: build rounds 0-2 of every deal, value the round-2 leaves
     with the surrogate at the round-3 roots, solve the three rounds batched, write out."""
-    cfg = P.pasur_config_default(iters=T)
+    cfg = P.pasur_config_default(iters=T, **SOLVER)
     b = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=_SUR["mlp"])
     u = b.pasur_batch_solve()
     ms, edges, _ = b.pasur_batch_stats()
@@ -422,6 +426,30 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def seed0_secondary(P, ctx, T, torch, stream, flush, steps: int = 5, warmup: int = 2):
+    """The seed-0 full game (3.4e7 FGT nodes), timed like the main workload: a secondary figure
+    beside a paper-scale headline deal."""
+    deck = P.pasur_deal(0)
+    _DECK_SEEDS[bytes(deck)] = 0
+    for _ in range(warmup):
+        solve_deal(P, ctx, deck, 0, T, True, torch)
+    ms, kms, upd = [], [], 0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        upd, k, _, _, _, _, _ = solve_deal(P, ctx, deck, 0, T, True, torch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kms.append(k)
+    m, km = statistics.mean(ms), statistics.mean(kms)
+    return {"seed": 0, "steps": steps, "warmup": warmup, "ms_per_step": m, "node_updates_per_step": upd,
+            "value": upd / (m / 1e3), "cfr_kernel_ms_per_step": km, "cfr_kernel_node_updates_per_s": upd / (km / 1e3),
+            "swept_node_updates_per_step": _WORK.get("swept"), "solved_node_updates_per_step": _WORK.get("solved")}
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -456,7 +484,7 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     launches0 = ctx.pasur_launch_count()
-    step_ms, kern_ms = [], []
+    step_ms, kern_ms, work = [], [], []
     updates = 0
     with ClockSampler(dev) as clk:
         torch.cuda.synchronize()
@@ -470,6 +498,7 @@ def run_ours(args, rank, world, dist):
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(kms)
+            work.append(dict(_WORK))
             updates = u
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
@@ -491,6 +520,9 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_mean = reduce_over_ranks(dist, statistics.mean(e2e_ms), "max", "cuda")
+    secondary = None
+    if args.workload == "full_game" and args.seed != 0 and world == 1:
+        secondary = seed0_secondary(P, ctx, T, torch, stream, flush)
 
     if rank != 0:
         return None
@@ -498,25 +530,40 @@ def run_ours(args, rank, world, dist):
     ms_per_step = total_ms / args.steps
     value = job_rate(job_updates, ms_per_step / 1e3)
     kernel_ms = statistics.mean(kern_ms)
+    solved = work[-1].get("solved", updates)
+    swept = work[-1].get("swept", updates)
     # dominant kernel: the CFR kernel (k_cfr_items, one launch per size class and round); the
-    # algorithmic traffic of CFR is the regret and strategy-sum read + write per node-update
-    ach_gbs = ALG_BYTES_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e9
+    # algorithmic traffic of CFR is the regret and strategy-sum read + write of every edge that
+    # carries CFR state, per iteration (the swept node-updates)
+    ach_gbs = ALG_BYTES_PER_UPDATE * swept / (kernel_ms / 1e3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     line = {
         "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded deals)",
-        "config": {"workload": f"{args.workload}: {desc}", "seed": args.seed, "iters_per_round": T,
+        "config": {"workload": f"{args.workload}: {desc}", "seed": args.seed, "iters_per_round": T, "solver": dict(SOLVER),
                    "fgt_sizes_per_round": info, "node_updates_per_step": updates,
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
-        "cfr_kernel": {"ms_per_step": kernel_ms, "node_updates_per_s": updates / (kernel_ms / 1e3)},
+        "cfr_kernel": {"ms_per_step": kernel_ms, "node_updates_per_s": updates / (kernel_ms / 1e3),
+                       "solved_node_updates_per_s": solved / (kernel_ms / 1e3),
+                       "swept_node_updates_per_s": swept / (kernel_ms / 1e3)},
+        "work": {"fgt_node_updates_per_step": updates, "solved_node_updates_per_step": solved,
+                 "swept_node_updates_per_step": swept,
+                 "solved_node_updates_per_s": job_rate(solved, ms_per_step / 1e3),
+                 "note": ("value counts every full-game-tree edge per iteration (the paper's FGT); the CFR solves "
+                          "one score slot per group of slots of a root that differ only in the inherited point "
+                          "difference (identical leaf values, so identical runs; results shared), and keeps "
+                          "state only for edges below nodes with more than one path (swept); forced-move chains "
+                          "are resolved once")},
         "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ach_gbs / hbm_peak,
                      "traffic": recorded_traffic(args.workload, args.seed),
                      "traffic_unit": "bytes per step (all k_cfr_items launches of one solve; ncu record in profiles/)",
-                     "note": (f"k_cfr_items; achieved = {ALG_BYTES_PER_UPDATE} B per node-update (R and S read + write) "
-                              f"x node-updates / CFR kernel time, peak = {src} HBM copy bandwidth; the kernel keeps "
-                              "each root's state in shared memory for all T iterations, so its DRAM traffic is far "
-                              "below the algorithmic bytes (ncu counters in profiles/) and it is issue/latency bound")},
+                     "note": (f"k_cfr_items; achieved = {ALG_BYTES_PER_UPDATE} B per swept node-update (R and S "
+                              f"read + write) x swept node-updates / CFR kernel time, peak = {src} HBM copy "
+                              "bandwidth; the kernel keeps each root's state in shared memory for all T "
+                              "iterations, so its DRAM traffic is far below the algorithmic bytes (ncu counters "
+                              "in profiles/): the fraction is an HBM-equivalent rate, the kernel is bound on chip "
+                              "(shared memory, issue, block barriers)")},
         "e2e": {"value": job_rate(job_updates, e2e_mean / 1e3), "unit": "node-updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(1, args.steps),
@@ -526,7 +573,10 @@ def run_ours(args, rank, world, dist):
             sp, note="games per deal through every solved round, moves drawn from the average "
                      "strategy with Philox4x64-10 (key = deal seed); inside each timed step"),
         "wall_s_timed": wall,
+        "device_memory_peak_bytes": int(ctx.memory()[1]),
     }
+    if secondary:
+        line["seed0_full_game"] = secondary
     if args.workload == "batch64" and _BATCH_SIZES:
         line["config"]["fgt_nodes_per_deal"] = size_histogram(_BATCH_SIZES)
     if args.workload == "surrogate16":
@@ -662,11 +712,22 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="full_game", choices=sorted(WORKLOADS))
-    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=None,
+                    help=f"deal seed (default: {FULL_GAME_SEED} for full_game, the first seed whose full game tree "
+                         "exceeds 1e9 nodes; 0 otherwise)")
     ap.add_argument("--iters", type=int, default=1000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots-per-item", type=int, default=0, help="pasur_config.slots_per_item (0 = automatic)")
+    ap.add_argument("--threads", type=int, default=0, help="pasur_config.threads (0 = per class)")
+    ap.add_argument("--no-merge", action="store_true", help="solve every score slot (pasur_config.merge_delta = 0)")
+    ap.add_argument("--stream-bytes", type=int, default=0,
+                    help="pasur_config.stream_bytes: roots needing more state stream over every SM (0 = default rule)")
     args = ap.parse_args()
+    if args.seed is None:
+        args.seed = FULL_GAME_SEED if args.workload == "full_game" else 0
+    SOLVER.update(slots_per_item=args.slots_per_item, threads=args.threads, merge_delta=0 if args.no_merge else 1,
+                  stream_bytes=args.stream_bytes)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -59,9 +59,11 @@ typedef struct {
  *                Umax = max |leaf value| in the subtree of the FGT root being solved (so each
  *                root's solve depends on its own subtree only), t = iteration index (1-based)
  *   dcfr_alpha/beta/gamma  DCFR discount exponents (the paper ran 1.5, 0, 2)
- *   slots_per_item  upper bound on the score slots solved together by one thread block (0 =
- *                choose automatically, at most 32); every block takes a power-of-two number of
- *                slots that fits its shared memory, results do not depend on the grouping
+ *   slots_per_item  score slots solved together by one thread block: 0 = automatic (the
+ *                smallest shared-memory class a root fits with one slot, then as many slots as
+ *                that class holds, at most 32); n > 0 = up to n (at most the root's own and 32),
+ *                in the smallest class that holds them.  Every block takes a power-of-two number
+ *                of slots; results do not depend on the grouping
  *   threads      threads per block of the CFR kernel (0 = choose per subtree size, else a
  *                multiple of 32 up to 1024)
  *   split_bytes  a root subtree whose state needs more shared memory than one block has is split
@@ -191,12 +193,31 @@ int pasur_export_level(const pasur_tree *tree, int k, int64_t cap, int64_t *pare
  * host or device).  EINVAL before that call. */
 int pasur_leaf_values(const pasur_tree *tree, float *out, int64_t cap);
 
+/* Convergence of the average strategy (section "Experimental Evaluation", figure "Convergence of
+ * CFR": the mean squared error of each intermediate average strategy to the final one, per round).
+ * Continues the CFR run of the tree (as pasur_cfr_iterate with cfg, cfg->iters ignored) up to each
+ * of the n iteration counts checkpoints[0] < ... < checkpoints[n-1] (counted from the start of the
+ * run; the first must exceed the iterations already done) and keeps the average strategy there.
+ * mse_out[i] (host, n doubles) = mean over every FGT edge (levels 1..8) of
+ * (sigma-bar after checkpoints[i] - sigma-bar after checkpoints[n-1])^2, so mse_out[n-1] = 0.
+ * next_root_util as in pasur_cfr_iterate.  Holds n copies of the average strategy of the solved
+ * slots on the device during the call.  Errors: EINVAL (checkpoints), ENOMEM, ENUMERIC. */
+int pasur_cfr_convergence(pasur_tree *tree, const pasur_config *cfg, const float *next_root_util,
+                          const int64_t *checkpoints, int n, double *mse_out);
+
 /* Work the CFR solve of a tree does (after its first pasur_cfr_iterate): solved_sizes (host, may be
  * NULL) receives the 9 FGT level sizes over the solved slots (cfg.merge_delta; equal to the FGT
  * sizes without merging), swept_edges (may be NULL) the (node, solved slot) pairs below the roots
  * that carry CFR state: the children of nodes with more than one path below them.  Every other
  * edge lies on a forced-move chain (average strategy 1, regret 0, never touched per iteration). */
 int pasur_solved_sizes(const pasur_tree *tree, int64_t solved_sizes[9], int64_t *swept_edges);
+
+/* How the CFR solves each GT root (after the first pasur_cfr_iterate; host out, cap >= GT roots):
+ * 0..4 = one thread block per item with the state in shared memory (size classes, smallest
+ * first), 5 = the level-streaming sweep over every SM with the state in device memory, 6 = a
+ * thread-block cluster (the subtree split over several SMs' shared memory), -1 = no CFR work
+ * (no score slot, or no move).  A diagnostic: results do not depend on the path. */
+int pasur_root_paths(const pasur_tree *tree, int32_t *path_out, int64_t cap);
 
 /* Timing of the last pasur_cfr_iterate call on the device (CUDA events around the CFR kernel
  * launches), the number of FGT edges, and the kernel launches it made. */

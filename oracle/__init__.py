@@ -77,6 +77,8 @@ def lib():
         L.or_next_roots.restype = C.c_int64
         L.or_leaf_utilities_linked.argtypes = [C.c_void_p, i64p, f64p, f64p]
         L.or_leaf_utilities_linked.restype = C.c_int
+        L.or_node_values.argtypes = [C.c_void_p, f64p, f64p, C.c_int, f64p]
+        L.or_node_values.restype = C.c_int
         L.or_cfr.argtypes = [C.c_void_p, f64p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                              C.c_double, f64p, f64p, f64p, f64p]
         L.or_cfr.restype = C.c_int
@@ -322,6 +324,16 @@ class Tree:
         if lib().or_cfr_f32(self._h, _p(lf, f64p), iters, tau, _p(sb, f64p), _p(U, f64p)) != 0:
             raise ValueError("or_cfr_f32 failed")
         return sb, U
+
+    def node_values(self, leaf, mode: int, sigma=None) -> list:
+        """Value of every FGT node under `mode` (as root_values), one array per level 0..8."""
+        q = self.sizes()[1]
+        out = np.zeros(int(q.sum()), np.float64)
+        lf = np.ascontiguousarray(leaf, np.float64)
+        sg = np.ascontiguousarray(sigma, np.float64) if sigma is not None else None
+        if lib().or_node_values(self._h, _p(lf, f64p), _p(sg, f64p), mode, _p(out, f64p)) != 0:
+            raise ValueError("or_node_values needs an unfolded tree")
+        return np.split(out, np.cumsum(q)[:-1])
 
     def root_values(self, leaf, mode: int, sigma=None) -> np.ndarray:
         """mode 0 minimax, 1 Alex best response to sigma, 2 Bob best response, 3 both sigma, 4 uniform."""

@@ -20,6 +20,8 @@
  *                                          edge's R and S after T = 1, 2, 3 by hand on a two-ply
  *                                          game, vanilla and DCFR(1.5, 0, 2))
  *   or_minimax / or_best_response          pinned (scipy LP on tiny subgames; BR_B <= v <= BR_A)
+ *   or_node_values                         pinned (level 0 equals or_root_values; every internal
+ *                                          node is its children's max / min / sigma-mean)
  *   or_philox4x64                          pinned (numpy's Philox bit generator, a library routine)
  *   or_selfplay                            pinned (sample mean and outcome frequencies against the
  *                                          exact values below; pure strategies give one game)
@@ -894,6 +896,52 @@ int or_root_values(const or_tree *t, const double *leaf, const double *sigma, in
     for (int64_t j = 0; j < t->n[0]; j++) {
         int64_t S = t->fgt_off[0][j + 1] - t->fgt_off[0][j];
         for (int64_t s = 0; s < S; s++) out[t->fgt_off[0][j] + s] = value_rec(t, leaf, sig_lvl, mode, 0, j, s);
+    }
+    return 0;
+}
+
+/* Value of every FGT node under `mode` (see value_rec), levels 0..8 concatenated in FGT order
+ * (out has sum of the 9 level sizes entries): the same recursion as or_root_values, keeping each
+ * node's value.  Used by the tests to weigh a strategy difference at one node by the values of
+ * its children. */
+static double node_value_rec(const or_tree *t, const double *leaf, const double *sig_lvl[9], int mode, int k,
+                             int64_t j, int64_t s, double *const out_lvl[9]) {
+    double v;
+    if (k == 8) {
+        v = leaf[t->fgt_off[8][j] + s];
+    } else {
+        int d = t->nchild[k][j];
+        int p = k & 1;
+        int64_t cb = t->child_beg[k][j];
+        double best = 0.0, ev = 0.0;
+        for (int a = 0; a < d; a++) {
+            double c = node_value_rec(t, leaf, sig_lvl, mode, k + 1, cb + a, s, out_lvl);
+            if (a == 0 || (p == 0 ? c > best : c < best)) best = c;
+            double w = mode == 4 ? 1.0 / d : (sig_lvl[k + 1] ? sig_lvl[k + 1][t->fgt_off[k + 1][cb + a] + s] : 0.0);
+            ev += w * c;
+        }
+        v = mode == 0 ? best : mode == 1 ? (p == 0 ? best : ev) : mode == 2 ? (p == 1 ? best : ev) : ev;
+    }
+    out_lvl[k][t->fgt_off[k][j] + s] = v;
+    return v;
+}
+
+int or_node_values(const or_tree *t, const double *leaf, const double *sigma, int mode, double *out) {
+    if (!t->unfolded) return -1;
+    const double *sig_lvl[9] = {0};
+    double *out_lvl[9];
+    int64_t base = 0, sbase = 0;
+    for (int k = 0; k <= 8; k++) {
+        out_lvl[k] = out + base;
+        base += t->nq[k];
+        if (k >= 1 && sigma) {
+            sig_lvl[k] = sigma + sbase;
+            sbase += t->nq[k];
+        }
+    }
+    for (int64_t j = 0; j < t->n[0]; j++) {
+        int64_t S = t->fgt_off[0][j + 1] - t->fgt_off[0][j];
+        for (int64_t s = 0; s < S; s++) node_value_rec(t, leaf, sig_lvl, mode, 0, j, s, out_lvl);
     }
     return 0;
 }

@@ -542,6 +542,64 @@ int pasur_leaf_values(const pasur_tree *t, float *out, int64_t cap) {
     return rc;
 }
 
+int pasur_cfr_convergence(pasur_tree *t, const pasur_config *cfg, const float *next_root_util, const int64_t *checkpoints,
+                          int n, double *mse_out) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    pasur_ctx *ctx = t->ctx;
+    set_device(ctx);
+    if (!cfg || !checkpoints || !mse_out || n < 1) return set_err(ctx, PASUR_EINVAL, "pasur_cfr_convergence: bad arguments");
+    int64_t prev = t->iters_done;
+    for (int i = 0; i < n; i++) {
+        if (checkpoints[i] <= prev || checkpoints[i] - prev > INT32_MAX)
+            return set_err(ctx, PASUR_EINVAL, "pasur_cfr_convergence: checkpoints must increase past the iterations done");
+        prev = checkpoints[i];
+    }
+    std::vector<float *> snap((size_t)n, nullptr);
+    double *acc = nullptr;
+    size_t sb = 0;
+    int rc = PASUR_OK;
+    auto release = [&]() {
+        for (float *p : snap)
+            if (p) dev_free(ctx, p, sb);
+        if (acc) dev_free(ctx, acc, sizeof(double) * (size_t)n);
+    };
+    for (int i = 0; i < n && rc == PASUR_OK; i++) {
+        pasur_config c = *cfg;
+        c.iters = (int32_t)(checkpoints[i] - t->iters_done);
+        rc = pasur_cfr_iterate(t, &c, next_root_util);
+        if (rc != PASUR_OK) break;
+        if (!sb) {
+            int64_t ce = 0;
+            for (int k = 1; k < 9; k++) ce += t->cQ[k];
+            sb = sizeof(float) * (size_t)(ce + 1);
+        }
+        rc = dev_alloc(ctx, (void **)&snap[(size_t)i], sb);
+        if (rc == PASUR_OK) rc = export_sigma_solved(t, snap[(size_t)i]);
+    }
+    if (rc == PASUR_OK) rc = dev_alloc(ctx, (void **)&acc, sizeof(double) * (size_t)n);
+    if (rc == PASUR_OK && cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)n, ctx->stream) != cudaSuccess)
+        rc = set_err(ctx, PASUR_ECUDA, "pasur_cfr_convergence: memset");
+    for (int i = 0; i < n && rc == PASUR_OK; i++) rc = sigma_sqdiff(t, snap[(size_t)i], snap[(size_t)(n - 1)], acc + i);
+    std::vector<double> h((size_t)n, 0.0);
+    if (rc == PASUR_OK && (cudaMemcpyAsync(h.data(), acc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                           cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+        rc = set_err(ctx, PASUR_ECUDA, "pasur_cfr_convergence: read back");
+    release();
+    if (rc != PASUR_OK) return rc;
+    int64_t ne = 0;
+    for (int k = 1; k < 9; k++) ne += t->Q[k];
+    for (int i = 0; i < n; i++) mse_out[i] = ne > 0 ? h[(size_t)i] / (double)ne : 0.0;
+    return PASUR_OK;
+}
+
+int pasur_root_paths(const pasur_tree *t, int32_t *path_out, int64_t cap) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    if (!t->cfr_ready) return set_err(t->ctx, PASUR_EINVAL, "pasur_root_paths: no CFR run yet");
+    if (!path_out || cap < t->n_roots) return set_err(t->ctx, PASUR_EOVERFLOW, "pasur_root_paths: cap < GT roots");
+    for (int64_t g = 0; g < t->n_roots; g++) path_out[g] = t->croots_h[(size_t)g].cls;
+    return PASUR_OK;
+}
+
 int pasur_solved_sizes(const pasur_tree *t, int64_t solved_sizes[9], int64_t *swept_edges) {
     if (check_tree(t)) return PASUR_EINVAL;
     if (!t->cfr_ready) return set_err(t->ctx, PASUR_EINVAL, "pasur_solved_sizes: no CFR run yet");

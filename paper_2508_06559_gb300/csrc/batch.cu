@@ -239,7 +239,7 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
         CfrPlan one = plan;
         for (int o = 0; o < 8; o++)
             if (o != c) one.cls_begin[o] = one.cls_end[o] = 0;
-        for (int o = 0; o < 3; o++) one.clu_begin[o] = one.clu_end[o] = 0;
+        for (int o = 0; o < kCluGroups; o++) one.clu_begin[o] = one.clu_end[o] = 0;
         float best_ms = 1e30f;
         int best = def;
         for (int i = 0; i < 3; i++) {
@@ -328,7 +328,7 @@ int print_batch(pasur_batch *b) {
             PASUR_TRY(cfr_export_utilities_n(tree_of(b, d, ri), b->cfg.iters, b->util[(size_t)(d * b->n_rounds + ri)]));
         fprintf(stderr, "[pasur] batch round %d: %lld items, %d iterations in %.3f ms\n", b->first_round + ri,
                 (long long)pl.n_items, b->cfg.iters, ms);
-        for (int bk = 0; bk < 3; bk++)
+        for (int bk = 0; bk < kCluGroups; bk++)
             if (pl.clu_end[bk] != pl.clu_begin[bk])
                 fprintf(stderr, "[pasur]   cluster items: %lld, %d CTAs x %d threads, smem %zu B, %.3f ms\n",
                         (long long)(pl.clu_end[bk] - pl.clu_begin[bk]), pl.clu_ctas[bk], pl.clu_threads, pl.clu_smem[bk],

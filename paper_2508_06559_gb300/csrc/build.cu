@@ -528,6 +528,15 @@ int plan_solve_slots(pasur_tree *t, bool merge, const float *next_util_dev) {
     }
     t->merged = any;
     t->csoff_h = csoff;
+    {
+        // full slots per solved slot (the weight of a solved slot in averages over the FGT)
+        std::vector<int32_t> mult((size_t)csoff[(size_t)nr] + 1, 0);
+        for (int64_t q = 0; q < q0; q++) mult[(size_t)cidx0[(size_t)q]]++;
+        PASUR_TRY(tree_alloc(t, (void **)&t->cmult_d, sizeof(int32_t) * mult.size()));
+        PASUR_CUDA(ctx, cudaMemcpyAsync(t->cmult_d, mult.data(), sizeof(int32_t) * mult.size(), cudaMemcpyHostToDevice,
+                                        ctx->stream));
+        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     if (!any) {
         for (int k = 0; k < 9; k++) {
             t->cfgt_off[k] = t->fgt_off[k];

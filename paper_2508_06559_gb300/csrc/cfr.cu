@@ -37,8 +37,10 @@ constexpr int kClsGlobal = kNumCls - 1;
 constexpr int kClsCluster = 6;       // plan class of the cluster items' pseudo-items (exports only)
 constexpr int kMaxClusterCtas = 16;  // CTAs of a cluster (16: non-portable size)
 // default block size per class (the batch autotuner measures its own); class 3 at two 256-thread
-// blocks per SM measured faster than one 512-thread block of the 512-thread instantiation
-constexpr int kClsThreads[kNumCls] = {128, 128, 256, 256, 1024, 1024};
+// blocks per SM measured faster than one 512-thread block of the 512-thread instantiation, and
+// class 4 (one block per SM) faster at 256 than at 1024 threads (fewer warps idle at the level
+// barriers: seed-47 final round 306 -> 293 ms)
+constexpr int kClsThreads[kNumCls] = {128, 128, 256, 256, 256, 1024};
 
 struct CfrParams {
     const CfrItem *items;
@@ -885,6 +887,34 @@ __global__ void k_export_util(const double *uacc, const int64_t *cidx0, int64_t 
         out[i] = (float)(uacc[cidx0[i]] * inv_t);
 }
 
+// One level of sum_e m_e (a_e - b_e)^2 over the solved edges e of the level (m_e: full slots that
+// solved slot stands for), one warp per GT node, lanes over its solved slots; block sums in f64
+// added to *acc.
+__global__ void k_sigma_sqdiff(const int32_t *__restrict__ root, int64_t m, const int64_t *__restrict__ cfgt_off,
+                               const int64_t *__restrict__ csoff, const int32_t *__restrict__ cmult,
+                               const float *__restrict__ a, const float *__restrict__ b, double *acc) {
+    __shared__ double part[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double sum = 0.0;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        const int32_t g = root[j];
+        const int64_t c0 = cfgt_off[j], ns = cfgt_off[j + 1] - c0, w0 = csoff[g];
+        for (int64_t x = lane; x < ns; x += 32) {
+            const double d = (double)a[c0 + x] - (double)b[c0 + x];
+            sum += (double)cmult[w0 + x] * d * d;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    if (lane == 0) part[wid] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += part[i];
+        atomicAdd(acc, s);
+    }
+}
+
 // One level of the average strategies of every full slot from those of the solved slots: one warp
 // per GT node j, lanes over its full slots (consecutive output addresses); full slot s of root g
 // reads solved slot cidx0[score_off[g] + s] - csoff[g] of the same node.
@@ -1475,14 +1505,20 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
             }
             continue;
         }
+        // slots per item: a power of two (the kernel indexes slots with shifts).  Automatic: the
+        // smallest class the root fits with one slot, then the largest count that class holds.
+        // With cfg.slots_per_item: that many slots (at most the root's), in the smallest class
+        // that holds them, fewer where no class does.
+        int64_t want = 1;
+        if (cfg->slots_per_item > 0)
+            while (want * 2 <= std::min<int64_t>(Sg, wcap)) want *= 2;
         int cls = kClsGlobal;
-        for (int c = 0; c < kNumCls - 1 && !streamed[(size_t)g]; c++)
-            if (resident_bytes(L, nA, 1) <= budget[c]) {
-                cls = c;
-                break;
-            }
-        // slots per item: a power of two (the kernel indexes slots with shifts), the largest that
-        // fits the class; the remaining slots of the root go to power-of-two items too
+        for (; want >= 1 && cls == kClsGlobal && !streamed[(size_t)g]; want /= 2)
+            for (int c = 0; c < kNumCls - 1; c++)
+                if (resident_bytes(L, nA, want) <= budget[c]) {
+                    cls = c;
+                    break;
+                }
         int64_t w = 1;
         while (w * 2 <= std::min<int64_t>(Sg, wcap) && (cls == kClsGlobal || resident_bytes(L, nA, w * 2) <= budget[cls])) w *= 2;
         cr.W = (int32_t)w;
@@ -1612,12 +1648,12 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
     plan.clu_h = clu;
     std::stable_sort(plan.clu_h.begin(), plan.clu_h.end(),
                      [](const ClusterItem &a, const ClusterItem &b) { return a.nparts < b.nparts; });
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < kCluGroups; b++) {
         plan.clu_begin[b] = plan.clu_end[b] = 0;
         plan.clu_smem[b] = 0;
     }
     int64_t i = 0;
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < kCluGroups; b++) {
         plan.clu_begin[b] = i;
         while (i < (int64_t)plan.clu_h.size() && plan.clu_h[(size_t)i].nparts <= plan.clu_ctas[b]) {
             plan.clu_smem[b] = std::max(plan.clu_smem[b], (size_t)plan.clu_h[(size_t)i].smem);
@@ -1625,11 +1661,9 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         }
         plan.clu_end[b] = i;
     }
-    // one block width for the cluster launches: 1024 threads when a part fills an SM's shared
-    // memory, narrower when several parts can share an SM
-    size_t cmax = 0;
-    for (int b = 0; b < 3; b++) cmax = std::max(cmax, plan.clu_smem[b]);
-    plan.clu_threads = cmax <= 72 * 1024 ? 256 : (cmax <= 112 * 1024 ? 512 : 1024);
+    // one block width for the cluster launches: 256 threads (a part's level steps are short;
+    // on the seed-47 final round 256 threads measured faster than 1024: 1096 -> 1071 ms)
+    plan.clu_threads = 256;
     if (cfg->threads > 0) plan.clu_threads = cfg->threads;
     if (!plan.clu_h.empty()) {
         size_t b = sizeof(ClusterItem) * plan.clu_h.size();
@@ -1741,7 +1775,7 @@ int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float 
 int ensure_aux(pasur_ctx *ctx) {
     if (ctx->fork) return PASUR_OK;
     PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
-    for (int c = 0; c < kClsCluster + 3; c++) {
+    for (int c = 0; c < kClsCluster + kCluGroups; c++) {
         PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
         PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
         PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
@@ -1819,7 +1853,7 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
     }
     // roots split over thread-block clusters: one cluster per item, a launch (and a stream) per
     // cluster size
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < kCluGroups; b++) {
         const int64_t n = plan.clu_end[b] - plan.clu_begin[b];
         if (n == 0) continue;
         const int c = kClsCluster + b;
@@ -1871,7 +1905,7 @@ int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg) {
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < kCluGroups; b++) {
         if (plan->clu_end[b] == plan->clu_begin[b]) continue;
         if (plan->clu_smem[b] > lim) return set_err(ctx, PASUR_EINVAL, "cluster part exceeds the shared memory of a block");
         cudaLaunchConfig_t lc{};
@@ -1900,7 +1934,7 @@ void cfr_plan_times(pasur_ctx *ctx, CfrPlan &plan) {
         if (plan.cls_end[c] != plan.cls_begin[c]) cudaEventElapsedTime(&m, ctx->cls_t0[c], ctx->cls_t1[c]);
         plan.cls_ms[c] = m;
     }
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < kCluGroups; b++) {
         float m = 0.f;
         if (plan.clu_end[b] != plan.clu_begin[b]) cudaEventElapsedTime(&m, ctx->cls_t0[kClsCluster + b], ctx->cls_t1[kClsCluster + b]);
         plan.cls_ms[kClsCluster + b] = m;
@@ -1915,19 +1949,32 @@ static void print_plan(const pasur_tree *t, const CfrPlan &plan) {
     for (int c = 0; c < kNumCls; c++) {
         int64_t n = plan.cls_end[c] - plan.cls_begin[c];
         if (!n) continue;
-        int64_t cost = 0, maxcost = 0;
+        int64_t cost = 0, maxcost = 0, swept = 0, slots = 0;
         for (int64_t i = plan.cls_begin[c]; i < plan.cls_end[c]; i++) {
-            cost += plan.items_h[(size_t)i].cost;
-            maxcost = std::max(maxcost, plan.items_h[(size_t)i].cost);
+            const CfrItem &it = plan.items_h[(size_t)i];
+            cost += it.cost;
+            maxcost = std::max(maxcost, it.cost);
+            swept += (int64_t)(t->croots_h[(size_t)it.root].ls[9] - 1) * it.ns;
+            slots += it.ns;
         }
-        fprintf(stderr, "[pasur]   class %d: items %lld, smem %zu B, blocks %d x %d threads, active-node-slots %lld "
-                        "(largest item %lld)\n",
-                c, (long long)n, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost, (long long)maxcost);
+        fprintf(stderr, "[pasur]   class %d: items %lld (slots %lld), smem %zu B, blocks %d x %d threads, active-node-slots "
+                        "%lld (largest item %lld), swept edges %lld\n",
+                c, (long long)n, (long long)slots, plan.cls_smem[c], plan.cls_blocks[c], plan.cls_threads[c], (long long)cost,
+                (long long)maxcost, (long long)swept);
     }
-    for (int b = 0; b < 3; b++)
-        if (plan.clu_end[b] != plan.clu_begin[b])
-            fprintf(stderr, "[pasur]   cluster items: %lld, %d CTAs x %d threads, smem %zu B\n",
-                    (long long)(plan.clu_end[b] - plan.clu_begin[b]), plan.clu_ctas[b], plan.clu_threads, plan.clu_smem[b]);
+    for (int b = 0; b < kCluGroups; b++)
+        if (plan.clu_end[b] != plan.clu_begin[b]) {
+            int64_t swept = 0, lmax = 0;
+            for (int64_t i = plan.clu_begin[b]; i < plan.clu_end[b]; i++) {
+                const int64_t L = t->croots_h[(size_t)plan.clu_h[(size_t)i].root].ls[9];
+                swept += L - 1;
+                lmax = std::max(lmax, L);
+            }
+            fprintf(stderr, "[pasur]   cluster items: %lld, %d CTAs x %d threads, smem %zu B, swept edges %lld (largest "
+                            "root %lld local nodes)\n",
+                    (long long)(plan.clu_end[b] - plan.clu_begin[b]), plan.clu_ctas[b], plan.clu_threads, plan.clu_smem[b],
+                    (long long)swept, (long long)lmax);
+        }
 }
 
 int cfr_prepare(pasur_tree *t, const pasur_config *cfg) {
@@ -1983,10 +2030,26 @@ int cfr_run(pasur_tree *t, const pasur_config *cfg) {
         fprintf(stderr, "[pasur] round %d: %d iterations in %.3f ms (", t->round, cfg->iters, ms);
         for (int c = 0; c < kNumCls; c++) fprintf(stderr, "%s%.2f", c ? " " : "", t->plan.cls_ms[c]);
         fprintf(stderr, " ms per class; clusters");
-        for (int b = 0; b < 3; b++) fprintf(stderr, " %.2f", t->plan.cls_ms[kClsCluster + b]);
+        for (int b = 0; b < kCluGroups; b++) fprintf(stderr, " %.2f", t->plan.cls_ms[kClsCluster + b]);
         fprintf(stderr, " ms)\n");
     }
     if (ef) return set_err(ctx, PASUR_ENUMERIC, "non-finite root value in the CFR sweep");
+    return PASUR_OK;
+}
+
+int sigma_sqdiff(const pasur_tree *t, const float *a_dev, const float *b_dev, double *acc_dev) {
+    pasur_ctx *ctx = t->ctx;
+    int64_t cb = 0;
+    for (int k = 1; k < 9; k++) {
+        if (t->M[k] > 0) {
+            const unsigned grid = (unsigned)std::min<int64_t>((t->M[k] * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+            k_sigma_sqdiff<<<grid, 256, 0, ctx->stream>>>(t->root[k], t->M[k], t->cfgt_off[k], t->csoff_d, t->cmult_d,
+                                                         a_dev + cb, b_dev + cb, acc_dev);
+            ctx->launches++;
+            PASUR_CUDA(ctx, cudaGetLastError());
+        }
+        cb += t->cQ[k];
+    }
     return PASUR_OK;
 }
 

@@ -131,7 +131,7 @@ struct pasur_ctx {
     int32_t *errflag = nullptr;  // device error word
     int64_t launches = 0;        // kernels launched through this context
     // forked streams for concurrent launches (created on first use): CFR classes 0..5, cluster
-    // launches 6..8
+    // launches 6..9
     cudaStream_t aux[12] = {nullptr};
     cudaEvent_t fork = nullptr, join[12] = {nullptr}, cls_t0[12] = {nullptr}, cls_t1[12] = {nullptr};
     int64_t live_trees = 0;      // trees not yet freed (the context outlives them)
@@ -215,6 +215,9 @@ struct CfrItem {              // one work item of the CFR kernel: a root and a r
     int64_t cost;             // active nodes * slots, for the schedule
 };
 
+// cluster items are launched in groups by their CTA count: clusters of 2, 4, 8 and 16 CTAs
+constexpr int kCluGroups = 4;
+
 // A CFR launch plan: work items of one or more trees merged per shared-memory class.
 struct CfrPlan {
     std::vector<CfrItem> items_h;       // ordered by class, then cost (largest first)
@@ -227,13 +230,13 @@ struct CfrPlan {
     int cls_threads[8] = {0};
     float cls_ms[12] = {0};
     // cluster items (class 6 holds their pseudo-items, used for exports only), sorted by part
-    // count into up to three launches of 4, 8 and 16 CTAs per cluster
+    // count into up to four launches of 2, 4, 8 and 16 CTAs per cluster
     std::vector<ClusterItem> clu_h;
     ClusterItem *clu_d = nullptr;
     int clu_threads = 0;
-    int64_t clu_begin[3] = {0}, clu_end[3] = {0};
-    int clu_ctas[3] = {4, 8, 16};
-    size_t clu_smem[3] = {0};
+    int64_t clu_begin[kCluGroups] = {0}, clu_end[kCluGroups] = {0};
+    int clu_ctas[kCluGroups] = {2, 4, 8, 16};
+    size_t clu_smem[kCluGroups] = {0};
     // items of class 5 (state in device memory) run as a level-streaming sweep over every SM:
     // exclusive prefixes over those items of their (entry, slot) pairs per level [8][n + 1], of
     // their (local node, slot) pairs [n + 1] and of their slots [n + 1]; per slot the largest
@@ -279,6 +282,7 @@ struct pasur_tree {
     int64_t *csoff_d = nullptr;
     int32_t *crep_d = nullptr;          // [cQ[0]] per solved slot: its first full slot within the root
     int64_t *cidx0_d = nullptr;         // [Q[0]] per full root slot: the global index of its solved slot
+    int32_t *cmult_d = nullptr;         // [cQ[0]] per solved slot: the number of full slots it stands for
     int64_t *cfgt_off[9] = {nullptr};   // per GT node: first solved FGT node (= fgt_off unless merged)
     int64_t cQ[9] = {0};                // solved FGT level sizes
     int64_t swept_edges = 0;            // (local non-root node, solved slot) pairs: edges with CFR state
@@ -386,6 +390,11 @@ int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float 
 // blocks of a persistent CFR launch with this block size and shared memory (0 if it cannot run)
 int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks);
 int cfr_export_sigma(const pasur_tree *t, float *out_dev);
+// average strategies of the solved slots only (levels 1..8, solved FGT order, sum of cQ[1..8])
+int export_sigma_solved(const pasur_tree *t, float *out_dev);
+// sum over every FGT edge of (a - b)^2 for two solved-order strategy vectors (each solved edge
+// counted once per full slot it stands for), added to *acc_dev (device double)
+int sigma_sqdiff(const pasur_tree *t, const float *a_dev, const float *b_dev, double *acc_dev);
 int cfr_export_utilities(const pasur_tree *t, float *out_dev);
 int cfr_export_utilities_n(const pasur_tree *t, int64_t iters, float *out_dev);
 int ensure_aux(pasur_ctx *ctx);

@@ -33,7 +33,8 @@ EXPORTS = [
     "pasur_mlp_forward", "pasur_mlp_gradients", "pasur_mlp_dataset_add_tree", "pasur_mlp_dataset_add_rows",
     "pasur_mlp_dataset_size", "pasur_mlp_dataset_export", "pasur_mlp_dataset_clear", "pasur_mlp_train",
     "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
-    "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work",
+    "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
+    "pasur_root_paths",
 ]
 
 
@@ -89,6 +90,8 @@ def load() -> C.CDLL:
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
     L.pasur_solved_sizes.argtypes = [vp, vp, i64p]
     L.pasur_batch_work.argtypes = [vp, i64p, i64p]
+    L.pasur_root_paths.argtypes = [vp, vp, i64]
+    L.pasur_cfr_convergence.argtypes = [vp, C.POINTER(pasur_config), vp, vp, C.c_int, vp]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
     L.pasur_batch_create_cut.argtypes = [vp, vp, i64, C.c_int, C.c_int, C.POINTER(pasur_config), vp, C.POINTER(vp)]
@@ -464,6 +467,23 @@ class Tree:
         q = np.zeros(9, np.int64)
         self._c(load().pasur_tree_sizes(self.h, _ptr(g), _ptr(q)))
         return g, q
+
+    def pasur_cfr_convergence(self, cfg: pasur_config, checkpoints, next_root_util=None) -> np.ndarray:
+        """MSE of the average strategy at each checkpoint (iteration counts) to the last one."""
+        cp = np.ascontiguousarray(checkpoints, np.int64)
+        out = np.zeros(len(cp), np.float64)
+        nu = None
+        if next_root_util is not None:
+            nu = next_root_util if hasattr(next_root_util, "data_ptr") else np.ascontiguousarray(next_root_util, np.float32)
+        self._c(load().pasur_cfr_convergence(self.h, C.byref(cfg), _ptr(nu), _ptr(cp), len(cp), _ptr(out)))
+        return out
+
+    def pasur_root_paths(self) -> np.ndarray:
+        """Per GT root: 0..4 resident size class, 5 streamed, 6 cluster, -1 no CFR work."""
+        n = int(self.pasur_tree_sizes()[0][0])
+        out = np.zeros(max(n, 1), np.int32)
+        self._c(load().pasur_root_paths(self.h, _ptr(out), n))
+        return out[:n]
 
     def pasur_solved_sizes(self):
         """(solved FGT level sizes [9], swept edges) after the first pasur_cfr_iterate."""

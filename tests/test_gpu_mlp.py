@@ -117,6 +117,27 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
+BF16_ELEM_TOL = 2.0 ** -6
+
+
+def grad_scale(po, X, target):
+    """Per gradient element, the sum of the absolute values of the products that form it: the
+    backward pass of the oracle network carried out on absolute values (|dz|, |h|, |W|,
+    |gelu'|), the scale of a rounding-error bound for that element."""
+    y, c = M.forward(po, X, round_act=True)
+    n = len(y)
+    gy = np.abs(2.0 * (y - target) / n)
+    out = {"w3": c["h3"].T.__abs__() @ gy, "b3": np.array([gy.sum()])}
+    adh = np.outer(gy, np.abs(po["w3"]))
+    for l in (2, 1, 0):
+        adz = adh * np.abs(M.gelu_grad(c[f"z{l}"]))
+        out[f"b{l}"] = adz.sum(axis=0)
+        out[f"W{l}"] = adz.T @ np.abs(c[f"h{l}"])
+        if l:
+            adh = adz @ np.abs(po[f"W{l}"])
+    return out
+
+
 @pytest.mark.parametrize("n", [300, 1000])
 def test_gradients_match_oracle(ctx, n):
     from paper_2508_06559_gb300 import pasur as P
@@ -132,8 +153,14 @@ def test_gradients_match_oracle(ctx, n):
     le, ge, _ = M.loss_and_grads(M.unflatten(flat32.astype(np.float64)), X, Y.astype(np.float32).astype(np.float64))
     assert abs(loss - lo) <= 1e-3 * lo
     gg = M.unflatten(g.astype(np.float64))
+    scale = grad_scale(po, X, Y.astype(np.float32).astype(np.float64))
     for name, _ in M.SHAPES:
-        assert rel(gg[name], go[name]) <= 1e-2, (name, rel(gg[name], go[name]))
+        # element by element: every product that enters a gradient element may be off by one
+        # bf16 rounding of each operand (2^-8 relative) plus what earlier layers carried in; the
+        # bound is BF16_ELEM_TOL times the sum of the absolute values of those products
+        ratio = np.abs(gg[name] - go[name]) / (scale[name] + 1e-30)
+        print(f"{name}: max |g_gpu - g_oracle| / scale {ratio.max():.3e}, norm-relative {rel(gg[name], go[name]):.2e}")
+        assert (np.abs(gg[name] - go[name]) <= BF16_ELEM_TOL * scale[name] + 1e-12).all(), (name, float(ratio.max()))
         assert rel(gg[name], ge[name]) <= 3e-2, (name, rel(gg[name], ge[name]))
     mlp.free()
 

@@ -2,29 +2,28 @@
 
 Integer work (tree structure, states, running scores, unfolding, next roots, links, leaf values)
 must be bit-exact.  Floating point, after the same number of iterations:
-  - root utilities agree within 1e-5 (within 20x the oracle's own sensitivity to that noise where
-    it is larger: a root whose value moves under f32-sized leaf noise even in fp64);
+  - root utilities agree within U_TOL = 1e-5 absolute, no exception;
   - average strategies agree within 1e-4 absolute on every edge whose parent has own-reach mass
     sum_t pi_p^t(h) >= 1e-3 * T and is well conditioned: the oracle's own recursion carried out
     in float32, and oracle runs whose leaf values carry f32-sized noise (relative and absolute
-    1e-6, seeded: the size of f32 rounding compounded through the value recursion and the T
-    regret accumulations), each move that edge's average strategy by at most 1e-5.  At ill-conditioned parents (near-indifferent nodes, where regret matching flips
-    on noise of that size even in fp64) the difference must stay within 20x the oracle's own
-    sensitivity; at rarely reached parents the strategy must be a valid distribution.
+    1e-6, seeded), each move that edge's average strategy by at most 1e-5.
+  - at an ill-conditioned parent (a near-indifferent node, where regret matching flips on noise
+    of that size even in fp64, so the split between its moves is not fixed by the arithmetic)
+    an edge beyond 1e-4 needs value parity instead: swapping the oracle's average strategy at
+    that one node for the GPU's moves the round root's value under the oracle's average
+    strategies (the node's reach probability times the change of its own value, with the
+    oracle's on-policy values of its children) by at most VALUE_TOL = 1e-5.  The count of such
+    edges and parents, the largest strategy difference there and both value changes are
+    printed;
+  - at rarely reached parents the strategy must be a valid distribution.
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from tests.oracle_jobs import check_sigma, check_utilities, oracle_sensitivity, own_mass
 
 pytestmark = pytest.mark.gpu
-
-U_TOL = 1e-5
-SIGMA_TOL = 1e-4
-MASS_FRAC = 1e-3
-NOISE = 1e-6
-N_NOISE = 3
-COND_TOL = 1e-5
 
 
 def mask_ids(ids):
@@ -73,54 +72,6 @@ def unfold_both(gt, ot, score_off, scores):
     return q1
 
 
-def own_mass(ot, S):
-    """sum over children of S per FGT edge's parent, laid out per edge (levels 1..8)."""
-    q = ot.sizes()[1]
-    out = np.zeros_like(S)
-    base = 0
-    for k in range(1, 9):
-        par = ot.fgt_parents(k)
-        sums = np.bincount(par, weights=S[base:base + q[k]], minlength=int(q[k - 1]))
-        out[base:base + q[k]] = sums[par]
-        base += q[k]
-    return out
-
-
-def oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant=0, tau=1e-6):
-    """max |change| of every average strategy and root utility between the fp64 oracle run and
-    (a) the same oracle recursion carried out in float32, (b) oracle runs whose leaf values carry
-    f32-sized noise (relative and absolute NOISE, seeded signs)."""
-    rng = np.random.default_rng(20250806)
-    dp = np.zeros_like(sb_o)
-    du = np.zeros_like(U_o)
-    if variant == 0:
-        sb32, U32 = ot.cfr_f32(leaf_o, T, tau=tau)
-        dp = np.abs(sb32 - sb_o)
-        du = np.abs(U32 - U_o)
-    for _ in range(N_NOISE):
-        pert = leaf_o * (1 + NOISE * rng.choice([-1.0, 1.0], leaf_o.shape)) + NOISE * rng.choice([-1.0, 1.0], leaf_o.shape)
-        sb_p, U_p = ot.cfr(pert, T, tau=tau, variant=variant)
-        dp = np.maximum(dp, np.abs(sb_p - sb_o))
-        du = np.maximum(du, np.abs(U_p - U_o))
-    return dp, du
-
-
-def check_utilities(U_g, U_o, du):
-    d = np.abs(U_g - U_o)
-    assert (d <= np.maximum(U_TOL, 20 * du)).all(), (d.max(initial=0), du[np.argmax(d)] if len(d) else 0)
-
-
-def check_sigma(sb_g, sb_o, mass, dp, T):
-    assert np.isfinite(sb_g).all() and (sb_g >= 0).all() and (sb_g <= 1 + 1e-6).all()
-    d = np.abs(sb_g - sb_o)
-    heavy = mass >= MASS_FRAC * T
-    well = heavy & (dp <= COND_TOL)
-    ill = heavy & ~well
-    assert d[well].max(initial=0) <= SIGMA_TOL, (d[well].max(), int(np.argmax(np.where(well, d, 0))))
-    assert (d[ill] <= np.maximum(SIGMA_TOL, 20 * dp[ill])).all(), d[ill].max(initial=0)
-    return int(well.sum()), int(ill.sum())
-
-
 def compare_cfr(gt, ot, leaf_o, T, variant=0, next_util=None, tau=1e-6):
     cfg = P().pasur_config_default(iters=T, variant=variant, rm_deadzone=tau)
     gt.pasur_cfr_iterate(cfg, next_util)
@@ -129,9 +80,9 @@ def compare_cfr(gt, ot, leaf_o, T, variant=0, next_util=None, tau=1e-6):
     assert np.allclose(leaf_g, leaf_o, atol=1e-5, rtol=0)
     U_g = gt.pasur_round_utilities()
     sb_g = gt.pasur_avg_strategy()
-    dp, du = oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant, tau)
-    check_utilities(U_g, U_o, du)
-    check_sigma(sb_g, sb_o, own_mass(ot, S_o), dp, T)
+    dp, _ = oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant, tau)
+    du = check_utilities(U_g, U_o)
+    check_sigma(ot, leaf_o, sb_g, sb_o, own_mass(ot, S_o), dp, T, f" T={T} variant={variant} max|dU| {du:.2e}")
     return U_g, U_o, sb_g, sb_o
 
 

@@ -196,3 +196,30 @@ def test_dcfr_variant_converges(cfg1):
     br_b = t.root_values(leaf, O.BR_BOB, sb)[0]
     assert br_b - 1e-9 <= mm <= br_a + 1e-9
     assert (br_a - br_b) / 2 < 0.05
+
+
+def test_node_values_agree_with_root_values(cfg1):
+    """or_node_values keeps the value of every FGT node of the same recursion as or_root_values:
+    its level 0 is the root values (pinned above by the LP for mode 0), a leaf is its utility,
+    and each internal node is the max (Alex) / min (Bob) or sigma-mean of its children."""
+    _, t, leaf = cfg1
+    sb, _ = t.cfr(leaf, 50)
+    q = t.sizes()[1]
+    for mode in (O.MINIMAX, O.BR_ALEX, O.BR_BOB, O.ON_POLICY):
+        nv = t.node_values(leaf, mode, sb)
+        assert np.array_equal(nv[0], t.root_values(leaf, mode, sb))
+        assert np.array_equal(nv[8], leaf)
+        base = 0
+        for k in range(1, 9):
+            par = t.fgt_parents(k)
+            sig = sb[base:base + q[k]]
+            ev = np.bincount(par, weights=sig * nv[k], minlength=int(q[k - 1]))
+            mx = np.full(int(q[k - 1]), -np.inf)
+            mn = np.full(int(q[k - 1]), np.inf)
+            np.maximum.at(mx, par, nv[k])
+            np.minimum.at(mn, par, nv[k])
+            alex = (k - 1) % 2 == 0
+            want = {O.MINIMAX: mx if alex else mn, O.BR_ALEX: mx if alex else ev, O.BR_BOB: ev if alex else mn,
+                    O.ON_POLICY: ev}[mode]
+            assert np.allclose(nv[k - 1], want, rtol=0, atol=1e-12)
+            base += q[k]
