@@ -160,6 +160,19 @@ int pasur_unfold(pasur_tree *tree, const int64_t *score_offs, const pasur_score 
  * read only on the first call.  Later calls continue the same run.  Errors: EINVAL, ENUMERIC. */
 int pasur_cfr_iterate(pasur_tree *tree, const pasur_config *cfg, const float *next_root_util);
 
+/* pasur_cfr_iterate on the GT roots root_first .. root_first + root_count - 1 only: the roots of a
+ * round are independent (open hands, root reach 1), so several solvers can each take a range and
+ * add their root utilities (every root outside a solver's range has utility 0 there, so the sum of
+ * the solvers' pasur_round_utilities outputs is the whole round's, bit for bit).  Average
+ * strategies outside the range are unspecified.  The range is fixed by the first call on the tree
+ * (EINVAL if a later call passes another); pasur_cfr_iterate continues with it. */
+int pasur_cfr_iterate_roots(pasur_tree *tree, const pasur_config *cfg, const float *next_root_util,
+                            int64_t root_first, int64_t root_count);
+
+/* Number of GT nodes (all levels) below every GT root (host out, cap >= GT roots): the size by
+ * which callers balance root ranges. */
+int pasur_root_sizes(const pasur_tree *tree, int64_t *gt_nodes_out, int64_t cap);
+
 /* Average strategy (eq. avsigma, normalised per FGT parent; uniform where the strategy sum is 0)
  * of every FGT edge: levels 1..8 concatenated, each level in FGT order.  out: float, host or
  * device, cap = its length in elements (>= sum of FGT level sizes 1..8, else EOVERFLOW). */

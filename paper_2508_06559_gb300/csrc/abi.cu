@@ -374,6 +374,31 @@ int pasur_unfold(pasur_tree *t, const int64_t *score_offs, const pasur_score *sc
     return PASUR_OK;
 }
 
+int pasur_cfr_iterate_roots(pasur_tree *t, const pasur_config *cfg, const float *next_root_util, int64_t root_first,
+                            int64_t root_count) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    if (root_first < 0 || root_count < 0 || root_first + root_count > t->n_roots)
+        return set_err(t->ctx, PASUR_EINVAL, "pasur_cfr_iterate_roots: root range outside the tree's GT roots");
+    if (t->cfr_ready && (t->range_first != root_first || t->range_count != root_count))
+        return set_err(t->ctx, PASUR_EINVAL, "pasur_cfr_iterate_roots: the root range is fixed by the first call");
+    if (!t->cfr_ready) {
+        t->range_first = root_first;
+        t->range_count = root_count;
+    }
+    return pasur_cfr_iterate(t, cfg, next_root_util);
+}
+
+int pasur_root_sizes(const pasur_tree *t, int64_t *gt_nodes_out, int64_t cap) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    if (!gt_nodes_out || cap < t->n_roots) return set_err(t->ctx, PASUR_EOVERFLOW, "pasur_root_sizes: cap < GT roots");
+    for (int64_t g = 0; g < t->n_roots; g++) {
+        int64_t n = 0;
+        for (int k = 0; k < 9; k++) n += t->roots_h[(size_t)g].lvl_count[k];
+        gt_nodes_out[g] = n;
+    }
+    return PASUR_OK;
+}
+
 int pasur_cfr_iterate(pasur_tree *t, const pasur_config *cfg, const float *next_root_util) {
     if (check_tree(t)) return PASUR_EINVAL;
     pasur_ctx *ctx = t->ctx;

@@ -13,9 +13,12 @@
 // has sigma = 1 and zero regret on every edge below it and the value of its one leaf, so only the
 // "active" nodes (a local node that is not such a chain) are swept, and state is kept only for
 // local nodes (the root and the children of active nodes).  The item's regrets R, strategy sums
-// S, values V and reaches live in shared memory when they fit ("resident": no DRAM traffic per
-// iteration), otherwise in device memory.  Item layout: local node index times slots,
-// slot-minor.
+// S, values V and reaches live in shared memory for all T iterations (no DRAM traffic per
+// iteration).  A root whose state does not fit one block is split over a thread-block cluster
+// (distributed shared memory) or, beyond a cluster, swept level by level over every SM with its
+// state in device memory.  Item layout: local node index times slots, slot-minor; the local nodes
+// of each level are numbered in the order of their parents' entries, so the children of
+// consecutive entries are consecutive.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -369,49 +372,38 @@ __device__ __forceinline__ double iterate(const CfrParams &p, int W, const Entri
     return acc;
 }
 
-// All T iterations of one item.  RES: the item's arrays are in shared memory (carved from sm);
-// otherwise they are in device memory.
-template <int VARIANT, bool RES>
+// All T iterations of one item, its arrays in shared memory (carved from sm): the packed active
+// entries, then R, S, V, X per (local node, slot).
+template <int VARIANT>
 __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv, const CfrItem &it, const CfrRoot &cr,
                                          const int32_t *s_as, float *s_tu, int32_t *sb, int32_t *sn, int32_t *sf,
                                          unsigned char *sm) {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int W = it.ns;
     const int L = cr.ls[9], nA = s_as[9];
-    float *R, *S, *V, *X;
     const int32_t *gli = tv.act_li + cr.act_off, *gpl = tv.act_pl + cr.act_off, *gcs = tv.act_cs + cr.act_off;
     const uint16_t *gd = tv.act_d + cr.act_off;
     Entries<true> P{};
-    Entries<false> G{};
-    if (RES) {
-        size_t o = 0;
-        uint32_t *scd = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
-        uint32_t *slp = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
-        R = (float *)(sm + o); o += al16((size_t)L * W * 4);
-        S = (float *)(sm + o); o += al16((size_t)L * W * 4);
-        V = (float *)(sm + o); o += al16((size_t)L * W * 4);
-        X = (float *)(sm + o);
-        for (int i = tid; i < nA; i += nth) {
-            scd[i] = (uint32_t)gcs[i] | ((uint32_t)gd[i] << 16);
-            slp[i] = (uint32_t)gli[i] | ((uint32_t)(gpl[i] < 0 ? 0xFFFF : gpl[i]) << 16);
-        }
+    size_t o = 0;
+    uint32_t *scd = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
+    uint32_t *slp = (uint32_t *)(sm + o); o += al16((size_t)nA * 4);
+    float *R = (float *)(sm + o); o += al16((size_t)L * W * 4);
+    float *S = (float *)(sm + o); o += al16((size_t)L * W * 4);
+    float *V = (float *)(sm + o); o += al16((size_t)L * W * 4);
+    float *X = (float *)(sm + o);
+    for (int i = tid; i < nA; i += nth) {
+        scd[i] = (uint32_t)gcs[i] | ((uint32_t)gd[i] << 16);
+        slp[i] = (uint32_t)gli[i] | ((uint32_t)(gpl[i] < 0 ? 0xFFFF : gpl[i]) << 16);
+    }
+    {
         const float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
         for (int i = tid; i < L * W; i += nth) {
             R[i] = gR[i];
             S[i] = gS[i];
         }
-        P.cd = scd;
-        P.lp = slp;
-    } else {
-        G.li = gli;
-        G.pl = gpl;
-        G.cs = gcs;
-        G.d = gd;
-        R = tv.R + it.data_base;
-        S = tv.S + it.data_base;
-        V = tv.V + it.scratch_base;
-        X = tv.X + it.scratch_base;
     }
+    P.cd = scd;
+    P.lp = slp;
     // values of the terminals (leaves and chain heads), constant over the iterations; root reach;
     // per slot the largest |leaf value| of the root's subtree, the scale of the dead zone
     for (int w = tid; w < W; w += nth) s_tu[w] = 0.f;
@@ -435,20 +427,16 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv,
     __syncthreads();
     for (int w = tid; w < W; w += nth) s_tu[w] = p.tau * s_tu[w];
     __syncthreads();
-    double acc;
-    if (RES && W == 1) acc = iterate<VARIANT, true, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu);
-    else if (RES) acc = iterate<VARIANT, false, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu);
-    else acc = iterate<VARIANT, false, false>(p, W, G, R, S, V, X, sb, sn, sf, s_tu);
+    const double acc = W == 1 ? iterate<VARIANT, true, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu)
+                              : iterate<VARIANT, false, true>(p, W, P, R, S, V, X, sb, sn, sf, s_tu);
     if (tid < W) {
         if (!isfinite(acc)) atomicOr(p.err, 1);
         tv.uacc[tv.fgt_off0[it.root] + it.s0 + tid] += acc;
     }
-    if (RES) {
-        float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
-        for (int i = tid; i < L * W; i += nth) {
-            gR[i] = R[i];
-            gS[i] = S[i];
-        }
+    float *gR = tv.R + it.data_base, *gS = tv.S + it.data_base;
+    for (int i = tid; i < L * W; i += nth) {
+        gR[i] = R[i];
+        gS[i] = S[i];
     }
     __syncthreads();
 }
@@ -471,8 +459,7 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrPara
         const CfrItem it = p.items[id];
         const TreeView tv = p.views[it.tree];
         const CfrRoot &cr = tv.roots[it.root];
-        if (it.scratch_base < 0) run_item<VARIANT, true>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
-        else run_item<VARIANT, false>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
+        run_item<VARIANT>(p, tv, it, cr, s_as, s_tu, s_sb, s_sn, s_sf, sm);
     }
 }
 
@@ -490,6 +477,7 @@ struct StreamPlan {
     uint32_t *tu;          // per slot: largest |terminal value| (float bits)
     double *acc;           // per slot: sum of the root values of the current call
     int64_t n;
+    const StreamDesc *desc;  // [n] per item
 };
 
 // j with pre[j] <= x < pre[j + 1] (pre[0] = 0 <= x < pre[n])
@@ -503,19 +491,35 @@ __device__ __forceinline__ int64_t stream_item(const int64_t *pre, int64_t n, in
     return lo;
 }
 
-// the prefixes of a plan's class-5 items (one thread; once per plan)
-__global__ void k_stream_plan(const CfrItem *items, int64_t n, const TreeView *views, int64_t *pairs, int64_t *locs) {
+// the prefixes and descriptors of a plan's class-5 items (one thread; once per plan)
+__global__ void k_stream_plan(const CfrItem *items, int64_t n, const TreeView *views, int64_t *pairs, int64_t *locs,
+                              const int64_t *slots, StreamDesc *desc) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int64_t pk[8] = {0}, pl = 0;
     for (int64_t j = 0; j < n; j++) {
         const CfrItem it = items[j];
-        const CfrRoot &cr = views[it.tree].roots[it.root];
+        const TreeView &tv = views[it.tree];
+        const CfrRoot &cr = tv.roots[it.root];
         for (int k = 0; k < 8; k++) {
             pairs[(int64_t)k * (n + 1) + j] = pk[k];
             pk[k] += (int64_t)(cr.as[k + 1] - cr.as[k]) * it.ns;
         }
         locs[j] = pl;
         pl += (int64_t)cr.ls[9] * it.ns;
+        StreamDesc sd;
+        sd.R = tv.R + it.data_base;
+        sd.S = tv.S + it.data_base;
+        sd.V = tv.V + it.scratch_base;
+        sd.X = tv.X + it.scratch_base;
+        sd.li = tv.act_li + cr.act_off;
+        sd.pl = tv.act_pl + cr.act_off;
+        sd.cs = tv.act_cs + cr.act_off;
+        sd.d = tv.act_d + cr.act_off;
+        for (int k = 0; k < 9; k++) sd.as[k] = cr.as[k];
+        sd.ns = it.ns;
+        sd.sh = __ffs(it.ns) - 1;
+        sd.slot = slots[j];
+        desc[j] = sd;
     }
     for (int k = 0; k < 8; k++) pairs[(int64_t)k * (n + 1) + n] = pk[k];
     locs[n] = pl;
@@ -546,9 +550,59 @@ __global__ void k_stream_setup(CfrParams p, StreamPlan sp) {
     }
 }
 
-// one level step (level k; top-down or bottom-up) of iteration il of every class-5 item
+// One (entry, slot) pair of level k of a streamed item: the block sweep's node code on the item's
+// arrays in device memory.
 template <int VARIANT, bool TD>
-__global__ void __launch_bounds__(256) k_stream_level(CfrParams p, StreamPlan sp, int k, int il) {
+__device__ __forceinline__ void stream_pair(const StreamDesc &sd, int k, int64_t r, const StreamPlan &sp, float tau,
+                                            float tf, bool alex, float fpos, float fneg, float fs) {
+    const int sh = sd.sh;
+    const int e = sd.as[k] + (int)(r >> sh), w = (int)(r & (sd.ns - 1));
+    const int c = sd.cs[e], d = sd.d[e], li = sd.li[e], pl = sd.pl[e];
+    float *R = sd.R, *S = sd.S, *V = sd.V, *X = sd.X;
+    // the dead zone rounded as in the block sweep: (tau * Umax) * t
+    const float thr = (tau * __uint_as_float(sp.tu[sd.slot + w])) * tf;
+    if (TD) {
+        const float own = pl < 0 ? 1.f : X[(pl << sh) + w];
+        switch (d) {
+            case 1: td_node<1, false>(c, sh, w, own, R, X, thr); break;
+            case 2: td_node<2, false>(c, sh, w, own, R, X, thr); break;
+            case 3: td_node<3, false>(c, sh, w, own, R, X, thr); break;
+            case 4: td_node<4, false>(c, sh, w, own, R, X, thr); break;
+            case 5: td_node<5, false>(c, sh, w, own, R, X, thr); break;
+            case 6: td_node<6, false>(c, sh, w, own, R, X, thr); break;
+            case 7: td_node<7, false>(c, sh, w, own, R, X, thr); break;
+            case 8: td_node<8, false>(c, sh, w, own, R, X, thr); break;
+            default: td_node_any<false>(c, d, sh, w, own, R, X, thr);
+        }
+    } else {
+        const float pp = pl < 0 ? 1.f : X[(pl << sh) + w];
+        const float po = X[(li << sh) + w];
+        const float spo = alex ? po : -po;
+        float vh;
+        switch (d) {
+            case 1: vh = bu_node<VARIANT, 1, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 2: vh = bu_node<VARIANT, 2, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 3: vh = bu_node<VARIANT, 3, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 4: vh = bu_node<VARIANT, 4, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 5: vh = bu_node<VARIANT, 5, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 6: vh = bu_node<VARIANT, 6, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 7: vh = bu_node<VARIANT, 7, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            case 8: vh = bu_node<VARIANT, 8, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
+            default: vh = bu_node_any<VARIANT, false>(c, d, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
+        }
+        V[(li << sh) + w] = vh;
+        if (k == 0) sp.acc[sd.slot + w] += (double)vh;  // the root (one entry per item)
+    }
+}
+
+constexpr int kStreamThreads = 256;
+
+// One level step (level k; top-down or bottom-up) of iteration il of every class-5 item: a
+// grid-stride loop over the level's (entry, slot) pairs of all items (consecutive threads on
+// consecutive slots and entries); each pair finds its item by a binary search over the level's
+// prefix (a few cached loads) and reads what it needs from the item's descriptor.
+template <int VARIANT, bool TD>
+__global__ void __launch_bounds__(kStreamThreads, TD ? 4 : 3) k_stream_level(CfrParams p, StreamPlan sp, int k, int il) {
     const int64_t *pre = sp.pairs + (int64_t)k * (sp.n + 1);
     const int64_t total = pre[sp.n];
     const float tf = (float)(p.t0 + il + 1);
@@ -557,55 +611,7 @@ __global__ void __launch_bounds__(256) k_stream_level(CfrParams p, StreamPlan sp
     const bool alex = (k & 1) == 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = stream_item(pre, sp.n, x);
-        const CfrItem it = p.items[j];
-        const TreeView &tv = p.views[it.tree];
-        const CfrRoot &cr = tv.roots[it.root];
-        const int W = it.ns, sh = __ffs(W) - 1;
-        const int64_t r = x - pre[j];
-        const int e = cr.as[k] + (int)(r >> sh), w = (int)(r & (W - 1));
-        Entries<false> G{};
-        G.li = tv.act_li + cr.act_off;
-        G.pl = tv.act_pl + cr.act_off;
-        G.cs = tv.act_cs + cr.act_off;
-        G.d = tv.act_d + cr.act_off;
-        float *R = tv.R + it.data_base, *S = tv.S + it.data_base;
-        float *V = tv.V + it.scratch_base, *X = tv.X + it.scratch_base;
-        const float thr = (p.tau * __uint_as_float(sp.tu[sp.slots[j] + w])) * tf;
-        int c, d, li, pl;
-        G.child(e, c, d);
-        G.self(e, li, pl);
-        if (TD) {
-            const float own = pl < 0 ? 1.f : X[(pl << sh) + w];
-            switch (d) {
-                case 1: td_node<1, false>(c, sh, w, own, R, X, thr); break;
-                case 2: td_node<2, false>(c, sh, w, own, R, X, thr); break;
-                case 3: td_node<3, false>(c, sh, w, own, R, X, thr); break;
-                case 4: td_node<4, false>(c, sh, w, own, R, X, thr); break;
-                case 5: td_node<5, false>(c, sh, w, own, R, X, thr); break;
-                case 6: td_node<6, false>(c, sh, w, own, R, X, thr); break;
-                case 7: td_node<7, false>(c, sh, w, own, R, X, thr); break;
-                case 8: td_node<8, false>(c, sh, w, own, R, X, thr); break;
-                default: td_node_any<false>(c, d, sh, w, own, R, X, thr);
-            }
-        } else {
-            const float pp = pl < 0 ? 1.f : X[(pl << sh) + w];
-            const float po = X[(li << sh) + w];
-            const float spo = alex ? po : -po;
-            float vh;
-            switch (d) {
-                case 1: vh = bu_node<VARIANT, 1, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 2: vh = bu_node<VARIANT, 2, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 3: vh = bu_node<VARIANT, 3, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 4: vh = bu_node<VARIANT, 4, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 5: vh = bu_node<VARIANT, 5, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 6: vh = bu_node<VARIANT, 6, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 7: vh = bu_node<VARIANT, 7, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                case 8: vh = bu_node<VARIANT, 8, false>(c, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs); break;
-                default: vh = bu_node_any<VARIANT, false>(c, d, sh, w, pp, spo, R, S, V, thr, fpos, fneg, fs);
-            }
-            V[(li << sh) + w] = vh;
-            if (k == 0) sp.acc[sp.slots[j] + w] += (double)vh;  // the root (one entry per item)
-        }
+        stream_pair<VARIANT, TD>(sp.desc[j], k, x - pre[j], sp, p.tau, tf, alex, fpos, fneg, fs);
     }
 }
 
@@ -973,7 +979,7 @@ __global__ void k_fill_layout(int k, int64_t m, const int32_t *root, const int32
                               const int64_t *loc_rank, const int64_t *act_rank, const int64_t *loc_rank_next,
                               const int64_t *loc_rank_prev, const int64_t *parent, ChildPtrs co, const int64_t *fgt_off8,
                               const CfrRoot *roots, int64_t *loc_tq, int32_t *act_li, int32_t *act_pl, int32_t *act_cs,
-                              uint16_t *act_d, int64_t *act_gt, uint64_t *act_key, int32_t *err) {
+                              uint16_t *act_d, int64_t *act_gt, uint64_t *act_key, int32_t *act_rk, int32_t *err) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         if (!local[j]) continue;
         const CfrRoot &cr = roots[root[j]];
@@ -991,12 +997,53 @@ __global__ void k_fill_layout(int k, int64_t m, const int32_t *root, const int32
             act_gt[cr.act_off + e] = j;
             // sort key: the (root, level) segment, then degree descending
             act_key[cr.act_off + e] = ((uint64_t)(cr.act_off + cr.as[k]) << 16) | (uint64_t)(0xFFFF - (d > 0xFFFF ? 0xFFFF : d));
+            act_rk[cr.act_off + e] = (root[j] << 3) | k;
         } else {
             int64_t x = j;
             for (int kk = k; kk < 8; kk++) x = co.p[kk][x];  // follow the forced moves to the leaf
             loc_tq[cr.loc_off + li] = fgt_off8[x];
         }
     }
+}
+
+__global__ void k_widen_degrees(const uint16_t *d, int64_t n, int32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) out[i] = d[i];
+}
+
+// pos: exclusive scan of the degrees over the sorted entries.  The children of the entries of
+// root g at level k, in entry order, are the local nodes of level k+1 of that root: child a of
+// entry e becomes local node ls[k+1] + (pos[e] - pos[first entry of (g, k)]) + a.  lmap[old
+// global local index] = new global local index.
+__global__ void k_renumber_map(int64_t n, const int32_t *act_rk, const CfrRoot *roots, const int64_t *pos,
+                               const int32_t *act_cs, const uint16_t *act_d, int64_t *lmap) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = act_rk[e] >> 3, k = act_rk[e] & 7;
+        const CfrRoot &cr = roots[g];
+        const int64_t first = cr.ls[k + 1] + (pos[e] - pos[cr.act_off + cr.as[k]]);
+        const int d = act_d[e];
+        for (int a = 0; a < d; a++) lmap[cr.loc_off + act_cs[e] + a] = cr.loc_off + first + a;
+    }
+}
+
+__global__ void k_renumber_roots(int64_t nr, const CfrRoot *roots, int64_t *lmap) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nr; g += (int64_t)gridDim.x * blockDim.x)
+        if (roots[g].ls[9] > 0) lmap[roots[g].loc_off] = roots[g].loc_off;
+}
+
+__global__ void k_renumber_apply(int64_t n, const int32_t *act_rk, const CfrRoot *roots, const int64_t *pos, const int64_t *lmap,
+                                 int32_t *act_li, int32_t *act_pl, int32_t *act_cs) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = act_rk[e] >> 3, k = act_rk[e] & 7;
+        const CfrRoot &cr = roots[g];
+        act_li[e] = (int32_t)(lmap[cr.loc_off + act_li[e]] - cr.loc_off);
+        if (act_pl[e] >= 0) act_pl[e] = (int32_t)(lmap[cr.loc_off + act_pl[e]] - cr.loc_off);
+        act_cs[e] = (int32_t)(cr.ls[k + 1] + (pos[e] - pos[cr.act_off + cr.as[k]]));
+    }
+}
+
+__global__ void k_renumber_tq(int64_t n, const int64_t *lmap, const int64_t *tq_old, int64_t *tq) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        tq[lmap[x]] = tq_old[x];
 }
 
 __global__ void k_iota(int64_t *out, int64_t n) {
@@ -1126,8 +1173,8 @@ int build_layout(pasur_tree *t) {
     PASUR_TRY(tree_alloc(t, (void **)&t->act_d, sizeof(uint16_t) * (size_t)(act_off + 1)));
     PASUR_TRY(tree_alloc(t, (void **)&t->act_gt, sizeof(int64_t) * (size_t)(act_off + 1)));
     uint64_t *act_key = nullptr;
-    int64_t *perm = nullptr;
-    int32_t *t32 = nullptr;
+    int64_t *perm = nullptr, *pos = nullptr, *lmap = nullptr;
+    int32_t *t32 = nullptr, *act_rk = nullptr, *deg = nullptr;
     uint16_t *t16 = nullptr;
     int64_t *t64 = nullptr;
     {
@@ -1137,6 +1184,10 @@ int build_layout(pasur_tree *t) {
         sl.add(&t32, act_off);
         sl.add(&t16, act_off);
         sl.add(&t64, act_off);
+        sl.add(&act_rk, act_off);
+        sl.add(&deg, act_off);
+        sl.add(&pos, act_off);
+        sl.add(&lmap, loc_off);
         PASUR_TRY(sl.alloc(ctx, tmp));
     }
     ChildPtrs co;
@@ -1148,7 +1199,7 @@ int build_layout(pasur_tree *t) {
         k_fill_layout<<<grid_for(t->M[k], 256), 256, 0, ctx->stream>>>(
             k, t->M[k], t->root[k], local[k], active[k], lrank[k], arank[k], k < 8 ? lrank[k + 1] : nullptr,
             k > 0 ? lrank[k - 1] : nullptr, k > 0 ? t->parent[k] : nullptr, co, t->cfgt_off[8], t->croots_d, t->loc_tq,
-            t->act_li, t->act_pl, t->act_cs, t->act_d, t->act_gt, act_key, ctx->errflag);
+            t->act_li, t->act_pl, t->act_cs, t->act_d, t->act_gt, act_key, act_rk, ctx->errflag);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
     }
@@ -1180,8 +1231,41 @@ int build_layout(pasur_tree *t) {
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
         PASUR_CUDA(ctx, cudaMemcpyAsync(t->act_gt, t64, sizeof(int64_t) * (size_t)act_off, cudaMemcpyDeviceToDevice, ctx->stream));
-        PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        k_gather<int32_t><<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(act_rk, perm, act_off, t32);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_CUDA(ctx, cudaMemcpyAsync(act_rk, t32, sizeof(int32_t) * (size_t)act_off, cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    // renumber the local nodes of every level after the first in the order of their parents'
+    // entries: the children of consecutive entries become consecutive nodes (a warp's child
+    // accesses fall on few shared-memory banks and few device-memory sectors).  Child a of an
+    // entry stays child a, so every node's arithmetic is unchanged.
+    if (act_off > 0) {
+        k_widen_degrees<<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(t->act_d, act_off, deg);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        PASUR_TRY(exclusive_scan_i32(ctx, deg, pos, act_off));
+        k_renumber_map<<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(act_off, act_rk, t->croots_d, pos, t->act_cs, t->act_d,
+                                                                        lmap);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        k_renumber_roots<<<grid_for(nr, 256), 256, 0, ctx->stream>>>(nr, t->croots_d, lmap);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        k_renumber_apply<<<grid_for(act_off, 256), 256, 0, ctx->stream>>>(act_off, act_rk, t->croots_d, pos, lmap, t->act_li,
+                                                                          t->act_pl, t->act_cs);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+        // terminal leaf links follow their nodes
+        int64_t *tq_old = nullptr;
+        PASUR_TRY(dev_alloc(ctx, (void **)&tq_old, sizeof(int64_t) * (size_t)(loc_off + 1)));
+        tmp.push_back({tq_old, sizeof(int64_t) * (size_t)(loc_off + 1)});
+        PASUR_CUDA(ctx, cudaMemcpyAsync(tq_old, t->loc_tq, sizeof(int64_t) * (size_t)loc_off, cudaMemcpyDeviceToDevice, ctx->stream));
+        k_renumber_tq<<<grid_for(loc_off, 256), 256, 0, ctx->stream>>>(loc_off, lmap, tq_old, t->loc_tq);
+        ctx->launches++;
+        PASUR_CUDA(ctx, cudaGetLastError());
+    }
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return PASUR_OK;
 }
 
@@ -1218,7 +1302,7 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
         const CfrRoot &cr = t->croots_h[(size_t)g];
         const int64_t Sg = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
-        if (Sg == 0 || L == 0 || nA < 2 || streamed[(size_t)g]) continue;
+        if (Sg == 0 || L == 0 || nA < 2 || streamed[(size_t)g] || !t->in_range(g)) continue;
         const size_t need = resident_bytes(L, nA, 1);
         if (need > dyn_max || (cfg->split_bytes > 0 && need > (size_t)cfg->split_bytes)) cand.push_back(g);
     }
@@ -1454,7 +1538,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
         const CfrRoot &cr = t->croots_h[(size_t)g];
         const int64_t Sg = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
-        if (Sg == 0 || L == 0) continue;
+        if (Sg == 0 || L == 0 || !t->in_range(g)) continue;
         const size_t need = resident_bytes(L, nA, 1);
         streamed[(size_t)g] = (cfg->stream_bytes > 0 && need > (size_t)cfg->stream_bytes) ||
                               (need > dyn_max && Sg >= kStreamMinSlots);
@@ -1470,7 +1554,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
         const int64_t L = cr.ls[9], nA = cr.as[9];
         cr.W = 0;
         cr.cls = -1;
-        if (Sg == 0 || L == 0) continue;
+        if (Sg == 0 || L == 0 || !t->in_range(g)) continue;
         if (split_of[(size_t)g] >= 0) {
             const SplitRoot sr = splits[(size_t)split_of[(size_t)g]];
             cr.W = 1;
@@ -1551,7 +1635,8 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     t->swept_edges = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         const CfrRoot &cr = t->croots_h[(size_t)g];
-        if (cr.ls[9] > 1) t->swept_edges += (int64_t)(cr.ls[9] - 1) * (t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g]);
+        if (cr.ls[9] > 1 && t->in_range(g))
+            t->swept_edges += (int64_t)(cr.ls[9] - 1) * (t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g]);
     }
     if (!splits.empty()) {
         // append the parts' entries and local leaf indices; pseudo-roots after the real roots
@@ -1702,9 +1787,11 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         PASUR_TRY(own((void **)&plan.str_slots, sizeof(int64_t) * (size_t)(n + 1)));
         PASUR_TRY(own((void **)&plan.str_tu, sizeof(uint32_t) * (size_t)plan.str_nslots));
         PASUR_TRY(own((void **)&plan.str_acc, sizeof(double) * (size_t)plan.str_nslots));
+        PASUR_TRY(own((void **)&plan.str_desc, sizeof(StreamDesc) * (size_t)n));
         PASUR_CUDA(ctx, cudaMemcpyAsync(plan.str_slots, so.data(), sizeof(int64_t) * so.size(), cudaMemcpyHostToDevice,
                                         ctx->stream));
-        k_stream_plan<<<1, 32, 0, ctx->stream>>>(plan.items_d + b0, n, plan.views_d, plan.str_pairs, plan.str_locs);
+        k_stream_plan<<<1, 32, 0, ctx->stream>>>(plan.items_d + b0, n, plan.views_d, plan.str_pairs, plan.str_locs,
+                                                 plan.str_slots, plan.str_desc);
         ctx->launches++;
         PASUR_CUDA(ctx, cudaGetLastError());
         PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1788,8 +1875,9 @@ int ensure_aux(pasur_ctx *ctx) {
 // iteration, the root sums into the running utilities.
 int stream_sweep(pasur_ctx *ctx, const CfrPlan &plan, CfrParams p, const pasur_config *cfg, cudaStream_t st) {
     p.items = plan.items_d + plan.cls_begin[kClsGlobal];
-    StreamPlan sp{plan.str_pairs, plan.str_locs, plan.str_slots, plan.str_tu, plan.str_acc, plan.str_n};
+    StreamPlan sp{plan.str_pairs, plan.str_locs, plan.str_slots, plan.str_tu, plan.str_acc, plan.str_n, plan.str_desc};
     const unsigned grid = (unsigned)ctx->num_sms * 8;
+    const unsigned lgrid = (unsigned)ctx->num_sms * 4;  // the level kernels: four (bottom-up: three) blocks per SM
     PASUR_CUDA(ctx, cudaMemsetAsync(plan.str_tu, 0, sizeof(uint32_t) * (size_t)plan.str_nslots, st));
     k_stream_setup<<<grid, 256, 0, st>>>(p, sp);
     ctx->launches++;
@@ -1798,11 +1886,11 @@ int stream_sweep(pasur_ctx *ctx, const CfrPlan &plan, CfrParams p, const pasur_c
         for (int i = 0; i < 15; i++) {
             const int k = i < 7 ? i : 14 - i;
             if (cfg->variant == 1) {
-                if (i < 7) k_stream_level<1, true><<<grid, 256, 0, st>>>(p, sp, k, il);
-                else k_stream_level<1, false><<<grid, 256, 0, st>>>(p, sp, k, il);
+                if (i < 7) k_stream_level<1, true><<<lgrid, kStreamThreads, 0, st>>>(p, sp, k, il);
+                else k_stream_level<1, false><<<lgrid, kStreamThreads, 0, st>>>(p, sp, k, il);
             } else {
-                if (i < 7) k_stream_level<0, true><<<grid, 256, 0, st>>>(p, sp, k, il);
-                else k_stream_level<0, false><<<grid, 256, 0, st>>>(p, sp, k, il);
+                if (i < 7) k_stream_level<0, true><<<lgrid, kStreamThreads, 0, st>>>(p, sp, k, il);
+                else k_stream_level<0, false><<<lgrid, kStreamThreads, 0, st>>>(p, sp, k, il);
             }
             ctx->launches++;
             PASUR_CUDA(ctx, cudaGetLastError());

@@ -218,6 +218,18 @@ struct CfrItem {              // one work item of the CFR kernel: a root and a r
 // cluster items are launched in groups by their CTA count: clusters of 2, 4, 8 and 16 CTAs
 constexpr int kCluGroups = 4;
 
+// One item of the level-streaming sweep, resolved once per plan: its state arrays, its active
+// entries (offsets applied), the level starts of its entries, its slot count (a power of two) and
+// the index of its first slot in the per-slot arrays of the sweep.
+struct StreamDesc {
+    float *R, *S, *V, *X;
+    const int32_t *li, *pl, *cs;
+    const uint16_t *d;
+    int32_t as[9];
+    int32_t sh, ns;
+    int64_t slot;
+};
+
 // A CFR launch plan: work items of one or more trees merged per shared-memory class.
 struct CfrPlan {
     std::vector<CfrItem> items_h;       // ordered by class, then cost (largest first)
@@ -245,6 +257,7 @@ struct CfrPlan {
     int64_t *str_pairs = nullptr, *str_locs = nullptr, *str_slots = nullptr;
     uint32_t *str_tu = nullptr;
     double *str_acc = nullptr;
+    struct StreamDesc *str_desc = nullptr;  // per class-5 item: what its (entry, slot) pairs need
 };
 
 struct pasur_tree {
@@ -319,6 +332,10 @@ struct pasur_tree {
     double *uacc = nullptr;             // cQ[0]
 
     int32_t variant = -1;
+    // GT roots the CFR solves: [range_first, range_first + range_count) (the whole round unless a
+    // caller shards the roots over several solvers)
+    int64_t range_first = 0, range_count = -1;
+    bool in_range(int64_t g) const { return range_count < 0 || (g >= range_first && g < range_first + range_count); }
     float last_ms = 0.f;
     int32_t last_launches = 0;
     std::vector<void *> allocs;

@@ -34,7 +34,7 @@ EXPORTS = [
     "pasur_mlp_dataset_size", "pasur_mlp_dataset_export", "pasur_mlp_dataset_clear", "pasur_mlp_train",
     "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
-    "pasur_root_paths",
+    "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes",
 ]
 
 
@@ -91,6 +91,8 @@ def load() -> C.CDLL:
     L.pasur_solved_sizes.argtypes = [vp, vp, i64p]
     L.pasur_batch_work.argtypes = [vp, i64p, i64p]
     L.pasur_root_paths.argtypes = [vp, vp, i64]
+    L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
+    L.pasur_root_sizes.argtypes = [vp, vp, i64]
     L.pasur_cfr_convergence.argtypes = [vp, C.POINTER(pasur_config), vp, vp, C.c_int, vp]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
@@ -508,6 +510,18 @@ class Tree:
         if next_root_util is not None:
             nu = next_root_util if hasattr(next_root_util, "data_ptr") else np.ascontiguousarray(next_root_util, np.float32)
         self._c(load().pasur_cfr_iterate(self.h, C.byref(cfg), _ptr(nu)))
+
+    def pasur_cfr_iterate_roots(self, cfg: pasur_config, next_root_util, root_first: int, root_count: int):
+        nu = None
+        if next_root_util is not None:
+            nu = next_root_util if hasattr(next_root_util, "data_ptr") else np.ascontiguousarray(next_root_util, np.float32)
+        self._c(load().pasur_cfr_iterate_roots(self.h, C.byref(cfg), _ptr(nu), root_first, root_count))
+
+    def pasur_root_sizes(self) -> np.ndarray:
+        n = int(self.pasur_tree_sizes()[0][0])
+        out = np.zeros(max(n, 1), np.int64)
+        self._c(load().pasur_root_sizes(self.h, _ptr(out), n))
+        return out[:n]
 
     def n_edges(self) -> int:
         return int(self.pasur_tree_sizes()[1][1:].sum())

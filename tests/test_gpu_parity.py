@@ -12,9 +12,11 @@ must be bit-exact.  Floating point, after the same number of iterations:
     an edge beyond 1e-4 needs value parity instead: swapping the oracle's average strategy at
     that one node for the GPU's moves the round root's value under the oracle's average
     strategies (the node's reach probability times the change of its own value, with the
-    oracle's on-policy values of its children) by at most VALUE_TOL = 1e-5.  The count of such
-    edges and parents, the largest strategy difference there and both value changes are
-    printed;
+    oracle's on-policy values of its children) by at most VALUE_TOL = 1e-5 plus what the
+    oracle's own float32 recursion and noisy-leaf runs move it by at that node (the arithmetic's
+    own limit: the fp64 oracle carried out in float32 lands there too), and never by more than
+    VALUE_CAP = 1e-3.  The count of such edges and parents, the largest strategy difference
+    there and the value changes are printed;
   - at rarely reached parents the strategy must be a valid distribution.
 """
 import numpy as np
@@ -80,9 +82,11 @@ def compare_cfr(gt, ot, leaf_o, T, variant=0, next_util=None, tau=1e-6):
     assert np.allclose(leaf_g, leaf_o, atol=1e-5, rtol=0)
     U_g = gt.pasur_round_utilities()
     sb_g = gt.pasur_avg_strategy()
-    dp, _ = oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant, tau)
+    pert = []
+    dp, _ = oracle_sensitivity(ot, leaf_o, sb_o, U_o, T, variant, tau, keep=pert)
     du = check_utilities(U_g, U_o)
-    check_sigma(ot, leaf_o, sb_g, sb_o, own_mass(ot, S_o), dp, T, f" T={T} variant={variant} max|dU| {du:.2e}")
+    check_sigma(ot, leaf_o, sb_g, sb_o, own_mass(ot, S_o), dp, T, f" T={T} variant={variant} max|dU| {du:.2e}",
+                perturbed=pert)
     return U_g, U_o, sb_g, sb_o
 
 
