@@ -35,11 +35,15 @@ WORKLOADS = {
     "final_round": (5, "final round of one seeded deal as a standalone round, score (0,0,0,0)"),
     "batch64": (3, "64 seeded deals (seeds S..S+63), rounds 4-6 (0-based 3-5) of each from the standalone root, "
                    "solved together: one merged persistent launch per round and size class under a CUDA graph"),
-    "surrogate16": (0, "16 seeded deals (seeds S..S+15): rounds 1-3 (0-based 0-2) solved in one batch with the "
-                       "leaves of round 3 valued by the trained surrogate at the round-4 roots (rounds 4-6 never "
-                       "built), against the exact batched solve of all six rounds"),
+    "surrogate64": (0, "64 seeded deals (seeds S..S+63): rounds 1-3 (0-based 0-2) solved in one batch with the "
+                       "leaves of round 3 valued by the trained surrogate at the round-4 roots, the round-4 roots "
+                       "the play reaches with probability above eps then solved exactly (rounds 4-6 from those "
+                       "roots only) and rounds 1-3 solved again, until no new root; against the exact batched solve "
+                       "of all six rounds"),
 }
-SUR_DEALS = 16
+SUR_DEALS = 64
+HYBRID_EPS = 1e-3       # the timed form's reach threshold
+HYBRID_FRONTIER = (None, 1e-2, 1e-3, 1e-4, 0.0)  # None = the surrogate alone
 SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..), rounds 4-6 from the standalone root
 SUR_LABEL_ITERS = 300
 BATCH_DEALS = 64
@@ -222,8 +226,11 @@ def no_learning_params(P):
 
 def surrogate_setup(P, ctx, decks, T, torch):
     """Untimed: train the surrogate on exact solves of other deals, solve the bench deals exactly
-    (batched, all six rounds, timed for the speedup), and measure the exploitability of the exact,
-    surrogate and no-learning profiles with the fp64 best-response chain."""
+    (batched, all six rounds, timed for the speedups), then the surrogate's cut at every eps of the
+    frontier (create + solve + exact-fallback passes, timed), each judged by the exploitability of
+    its whole-game profile (rounds 1-3 from the solve under test, rounds 4-6 exact; fp64
+    best-response chain over the six exact rounds)."""
+    from paper_2508_06559_gb300 import hybrid as H
     t0 = time.perf_counter()
     mlp = P.Mlp(ctx, dataset_capacity=2_000_000, seed=7)
     cfg_l = P.pasur_config_default(iters=SUR_LABEL_ITERS)
@@ -247,59 +254,57 @@ def surrogate_setup(P, ctx, decks, T, torch):
     torch.cuda.synchronize()
     exact_s = time.perf_counter() - t1
     _, exact_edges, _ = be.pasur_batch_stats()
-    # the surrogate at two cut points: after round 3 (rounds 1-3 solved; the timed form) and after
-    # round 4 (rounds 1-4 solved, the network values round-5 roots)
-    expl_exact = []
-    res = {}
-    cut_s = {}
-    for last in (2, 3):
+    te = [[be.pasur_batch_tree(d, r) for r in range(6)] for d in range(len(decks))]
+    br = [(P.chain_values(te[d], 1)[0], P.chain_values(te[d], 2)[0]) for d in range(len(decks))]
+    expl_exact = [(a - b) / 2 for a, b in br]
+
+    def judge(bs):
+        ex = []
+        for d in range(len(decks)):
+            sig = [bs.pasur_batch_tree(d, r).pasur_avg_strategy() for r in range(3)] + [None] * 3
+            ex.append((P.chain_values(te[d], 1, sig)[0] - P.chain_values(te[d], 2, sig)[0]) / 2)
+        return ex
+
+    frontier = []
+    for eps in HYBRID_FRONTIER:
         for key, net in (("surrogate", mlp), ("no_learning", none)):
+            if key == "no_learning" and eps is not None:
+                continue
             torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            bs = P.Batch(ctx, decks, 0, cfg, last_round=last, mlp=net)
-            bs.pasur_batch_solve()
-            torch.cuda.synchronize()
-            cut_s[(key, last)] = time.perf_counter() - t2
-            ex, mse = [], []
-            for d in range(len(decks)):
-                te = [be.pasur_batch_tree(d, r) for r in range(6)]
-                if last == 2 and key == "surrogate":
-                    expl_exact.append((P.chain_values(te, 1)[0] - P.chain_values(te, 2)[0]) / 2)
-                ts = [bs.pasur_batch_tree(d, r) for r in range(last + 1)]
-                sig = [t.pasur_avg_strategy() for t in ts] + [None] * (5 - last)
-                ex.append((P.chain_values(te, 1, sig)[0] - P.chain_values(te, 2, sig)[0]) / 2)
-                u_next = te[last + 1].pasur_round_utilities()
-                mse.append(float(((net.predict_next(ts[last]) - u_next) ** 2).mean()))
-            res[(key, last)] = (ex, mse)
+            if eps is None:
+                t2 = time.perf_counter()
+                bs = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
+                bs.pasur_batch_solve()
+                torch.cuda.synchronize()
+                st = dict(passes=0, exact_roots=0, wall_s=time.perf_counter() - t2)
+            else:
+                bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch)
+            ex = judge(bs)
             bs.free()
+            gap = float(np.mean(ex)) - float(np.mean(expl_exact))
+            frontier.append({"net": key, "eps": eps, "create_solve_s": st["wall_s"],
+                             "speedup_vs_exact": exact_s / st["wall_s"], "exploitability_mean": float(np.mean(ex)),
+                             "gap_vs_exact": gap, "max_deal_gap": float(np.max(np.array(ex) - np.array(expl_exact))),
+                             "passes": st["passes"], "exact_round4_roots": st["exact_roots"],
+                             "round4_roots": st.get("roots_after_cut")})
     be.free()
     none.free()
-    cuts = {}
-    for last in (2, 3):
-        cuts[f"rounds 1-{last + 1} solved, network at round-{last + 2} roots"] = {
-            "create_solve_s": {k: cut_s[(k, last)] for k in ("surrogate", "no_learning")},
-            "speedup_vs_exact": exact_s / cut_s[("surrogate", last)],
-            "exploitability_mean": {k: float(np.mean(res[(k, last)][0])) for k in ("surrogate", "no_learning")},
-            "exploitability_per_deal": {k: [round(float(x), 4) for x in res[(k, last)][0]] for k in ("surrogate", "no_learning")},
-            "root_value_mse": {k: float(np.mean(res[(k, last)][1])) for k in ("surrogate", "no_learning")}}
     _SUR.update(mlp=mlp, info={
-        "train_deals": SUR_TRAIN_DEALS, "train_rows": mlp.dataset_size(), "label_iters": SUR_LABEL_ITERS,
-        "data_gen_s": gen_s, "train_ms": train_ms, "adam_steps": steps, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+        "deals": len(decks), "train_deals": SUR_TRAIN_DEALS, "train_rows": mlp.dataset_size(),
+        "label_iters": SUR_LABEL_ITERS, "data_gen_s": gen_s, "train_ms": train_ms, "adam_steps": steps,
+        "train_loss_first_last": [float(losses[0]), float(losses[-1])],
         "exact_batch_s": exact_s, "exact_node_updates": exact_edges * T,
-        "exploitability_mean": {"exact": float(np.mean(expl_exact)),
-                                "surrogate": float(np.mean(res[("surrogate", 2)][0])),
-                                "no_learning": float(np.mean(res[("no_learning", 2)][0]))},
-        "exploitability_per_deal_exact": [round(float(x), 4) for x in expl_exact],
-        "cuts": cuts,
-        "target_gap": 1e-3})
+        "exploitability_mean_exact": float(np.mean(expl_exact)),
+        "frontier": frontier, "timed_eps": HYBRID_EPS, "target_gap": 1e-3})
 
 
 def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
-    """One step of the surrogate workload: build rounds 0-2 of every deal, value the round-2 leaves
-    with the surrogate at the round-3 roots, solve the three rounds batched, write out."""
+    """One step of the surrogate workload: rounds 1-3 of every deal batched with the surrogate at
+    the round-4 roots and the exact fallback for the roots reached with probability above
+    HYBRID_EPS; then every tree's average strategies and root utilities written out."""
+    from paper_2508_06559_gb300 import hybrid as H
     cfg = P.pasur_config_default(iters=T, **SOLVER)
-    b = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=_SUR["mlp"])
-    u = b.pasur_batch_solve()
+    b, st = H.solve_hybrid(P, ctx, decks, cfg, _SUR["mlp"], 0, 2, eps=HYBRID_EPS, torch=torch)
     ms, edges, _ = b.pasur_batch_stats()
     solved, swept = b.pasur_batch_work()
     _WORK.update(solved=solved * T, swept=swept * T)
@@ -322,8 +327,9 @@ def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, t
                 t.pasur_avg_strategy(sb)
             if d == 0:
                 info.append(q.tolist())
+    u0 = float(b.pasur_batch_tree(0, 0).pasur_round_utilities()[0])
     b.free()
-    return edges * T, ms, d2h, decks.nbytes, float(u[0]), info, None
+    return st["node_updates"], ms, d2h, decks.nbytes, u0, info, None
 
 
 class ClockSampler:
@@ -381,7 +387,7 @@ def rank_deal_seeds(workload: str, seed: int, rank: int):
     scaling, no collective on the data path)."""
     if workload == "batch64":
         return [seed + rank * BATCH_DEALS + i for i in range(BATCH_DEALS)]
-    if workload == "surrogate16":
+    if workload == "surrogate64":
         return [seed + rank * SUR_DEALS + i for i in range(SUR_DEALS)]
     return [seed + rank]
 
@@ -466,7 +472,7 @@ def run_ours(args, rank, world, dist):
     decks = np.stack([P.pasur_deal(s) for s in seeds])
     for s, dk in zip(seeds, decks):
         _DECK_SEEDS[bytes(dk)] = s
-    if args.workload == "surrogate16":
+    if args.workload == "surrogate64":
         deck = decks
         solve = solve_surrogate
         surrogate_setup(P, ctx, deck, T, torch)
@@ -579,14 +585,13 @@ def run_ours(args, rank, world, dist):
         line["seed0_full_game"] = secondary
     if args.workload == "batch64" and _BATCH_SIZES:
         line["config"]["fgt_nodes_per_deal"] = size_histogram(_BATCH_SIZES)
-    if args.workload == "surrogate16":
+    if args.workload == "surrogate64":
         si = dict(_SUR["info"])
-        si["surrogate_step_s"] = ms_per_step / 1e3
-        si["speedup_vs_exact"] = si["exact_batch_s"] / (ms_per_step / 1e3)
-        si["gap_vs_exact"] = si["exploitability_mean"]["surrogate"] - si["exploitability_mean"]["exact"]
-        si["note"] = ("exploitability = (BR_Alex - BR_Bob) / 2 of the whole-game profile (rounds 1-3 from the "
-                      "solve under test, rounds 4-6 exact), fp64 best-response chain over all six exact rounds; "
-                      "the speedup compares whole create+solve wall times of the two batched forms")
+        si["hybrid_step_s"] = ms_per_step / 1e3
+        si["speedup_vs_exact_timed"] = si["exact_batch_s"] / (ms_per_step / 1e3)
+        si["note"] = ("exploitability = (BR_Alex - BR_Bob) / 2 of the whole-game profile (rounds 1-3 from the solve "
+                      "under test, rounds 4-6 exact), fp64 best-response chain over all six exact rounds; speedups "
+                      "compare whole create+solve wall times of the batched forms; eps None = the surrogate alone")
         line["surrogate"] = si
     return line
 

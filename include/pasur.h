@@ -261,6 +261,22 @@ struct pasur_mlp;
 int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
                            const pasur_config *cfg, struct pasur_mlp *mlp, pasur_batch **out);
 
+/* pasur_batch_create with given roots: deal d's round first_round starts from the pools
+ * pools[deal_roots[d] .. deal_roots[d+1]) (strictly ascending per deal), pool i carrying the score
+ * slots scores[score_offs[i] .. score_offs[i+1]) (ascending, as for pasur_unfold); rounds
+ * first_round..5 are built and solved as in pasur_batch_create.  Roots are independent, so each
+ * root's utility equals its utility in a batch over all roots.  All arrays host;
+ * deal_roots: n_deals + 1 entries, score_offs: deal_roots[n_deals] + 1 entries. */
+int pasur_batch_create_roots(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const int64_t *deal_roots,
+                             const uint64_t *pools, const int64_t *score_offs, const pasur_score *scores,
+                             const pasur_config *cfg, pasur_batch **out);
+
+/* Replace the values the leaves of a cut batch's last round take at the roots after the cut
+ * (pasur_batch_create_cut: the surrogate's predictions): values (host or device, n floats, n =
+ * the number of roots pasur_next_roots gives for that deal's last tree) for deal `deal`.  The
+ * next pasur_batch_solve uses them (the solve graph reads the same buffer). */
+int pasur_batch_set_cut_values(pasur_batch *b, int64_t deal, const float *values, int64_t n);
+
 /* Solve the batch from scratch: cfg->iters CFR iterations per round, round 5 first, each round's
  * leaf values from the next round's average root utilities (eq. passuputil).  The first call
  * captures the whole backward sweep into a CUDA graph; every call replays it.  root_util_out
@@ -311,6 +327,14 @@ int pasur_batch_selfplay(pasur_batch *b, int64_t n_games, const uint64_t *seeds,
 int pasur_last_selfplay_stats(const pasur_ctx *ctx, float *ms, int64_t *games);
 
 /* ---- game values under fixed or optimal play (exploitability) ---------------------------- */
+/* Probability of reaching every next-round FGT root when both players follow sigma (NULL = the
+ * tree's own average strategy; else host or device, the pasur_avg_strategy layout) from the
+ * round's FGT roots with reach root_reach (double per FGT root, host or device; NULL = 1 each):
+ * the reach of every FGT leaf summed into its next root (t_lnk).  Chained over rounds it gives the
+ * probability of every later round's root under a strategy profile.  next_reach: double [next
+ * roots], host or device.  Non-final rounds after pasur_next_roots only. */
+int pasur_round_reach(pasur_tree *tree, const float *sigma, const double *root_reach, double *next_reach, int64_t cap);
+
 /* fp64 value of every FGT root of a round, from its leaves up: mode 0 minimax (Alex maximises,
  * Bob minimises), 1 Alex's best response to Bob's strategy, 2 Bob's best response to Alex's, 3 both
  * following the strategy.  Leaves as in pasur_cfr_iterate: final round = the round's difference

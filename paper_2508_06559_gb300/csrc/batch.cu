@@ -21,6 +21,11 @@ struct pasur_batch {
     pasur_ctx *ctx = nullptr;
     int first_round = 0, last_round = 5, n_rounds = 0;
     std::vector<float *> cut_util;        // per deal: surrogate values of the roots after last_round
+    // per deal: the roots of first_round (pools, score offsets, scores); empty = the standalone
+    // convention root (pool deck[0:4], score 0)
+    std::vector<std::vector<uint64_t>> root_pools;
+    std::vector<std::vector<int64_t>> root_soff;
+    std::vector<std::vector<pasur_score>> root_scores;
     int64_t n_deals = 0;
     std::vector<pasur_tree *> trees;      // [deal * n_rounds + (round - first_round)]
     std::vector<CfrPlan> plans;           // per round (index round - first_round)
@@ -76,6 +81,11 @@ int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, De
     std::vector<uint64_t> pools(1, pool0);
     std::vector<int64_t> soff = {0, 1};
     std::vector<pasur_score> scores(1, pasur_score{0, 0, 0, 0});
+    if (!b->root_pools.empty()) {
+        pools = b->root_pools[(size_t)d];
+        soff = b->root_soff[(size_t)d];
+        scores = b->root_scores[(size_t)d];
+    }
     for (int ri = 0; ri < b->n_rounds; ri++) {
         pasur_tree *t = nullptr;
         PASUR_TRY(pasur_build_round(wc, deck, b->first_round + ri, pools.data(), (int64_t)pools.size(), &t));
@@ -364,8 +374,42 @@ int pasur_batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, in
     return pasur_batch_create_cut(ctx, decks, n_deals, first_round, 5, cfg, nullptr, out);
 }
 
+static int batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
+                        const pasur_config *cfg, pasur_mlp *mlp, const int64_t *deal_roots, const uint64_t *pools,
+                        const int64_t *score_offs, const pasur_score *scores, pasur_batch **out);
+
 int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
                            const pasur_config *cfg, pasur_mlp *mlp, pasur_batch **out) {
+    return batch_create(ctx, decks, n_deals, first_round, last_round, cfg, mlp, nullptr, nullptr, nullptr, nullptr, out);
+}
+
+int pasur_batch_create_roots(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, const int64_t *deal_roots,
+                             const uint64_t *pools, const int64_t *score_offs, const pasur_score *scores,
+                             const pasur_config *cfg, pasur_batch **out) {
+    if (!deal_roots || !pools || !score_offs || !scores)
+        return ctx ? set_err(ctx, PASUR_EINVAL, "pasur_batch_create_roots: NULL argument") : PASUR_EINVAL;
+    return batch_create(ctx, decks, n_deals, first_round, 5, cfg, nullptr, deal_roots, pools, score_offs, scores, out);
+}
+
+int pasur_batch_set_cut_values(pasur_batch *b, int64_t deal, const float *values, int64_t n) {
+    if (!b) return PASUR_EINVAL;
+    pasur_ctx *ctx = b->ctx;
+    if (b->cut_util.empty()) return set_err(ctx, PASUR_EINVAL, "pasur_batch_set_cut_values: the batch has no cut");
+    if (deal < 0 || deal >= b->n_deals || !values) return set_err(ctx, PASUR_EINVAL, "pasur_batch_set_cut_values: bad deal or NULL");
+    const pasur_tree *t = b->trees[(size_t)(deal * b->n_rounds + b->n_rounds - 1)];
+    if (n != t->n_next_roots)
+        return set_err(ctx, PASUR_EINVAL, "pasur_batch_set_cut_values: n must be the number of roots after the cut (" +
+                                              std::to_string(t->n_next_roots) + ")");
+    cudaSetDevice(ctx->device);
+    PASUR_CUDA(ctx, cudaMemcpyAsync(b->cut_util[(size_t)deal], values, sizeof(float) * (size_t)n,
+                                    is_device_ptr(values) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PASUR_OK;
+}
+
+static int batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, int first_round, int last_round,
+                        const pasur_config *cfg, pasur_mlp *mlp, const int64_t *deal_roots, const uint64_t *pools,
+                        const int64_t *score_offs, const pasur_score *scores, pasur_batch **out) {
     if (!ctx || !out || !cfg || (n_deals > 0 && !decks)) return ctx ? set_err(ctx, PASUR_EINVAL, "pasur_batch_create: NULL argument") : PASUR_EINVAL;
     *out = nullptr;
     if (n_deals < 1 || n_deals > (1 << 20)) return set_err(ctx, PASUR_EINVAL, "pasur_batch_create: n_deals must be 1..2^20");
@@ -385,6 +429,30 @@ int pasur_batch_create_cut(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals
     b->cfg = *cfg;
     b->trees.assign((size_t)(n_deals * b->n_rounds), nullptr);
     b->util.assign(b->trees.size(), nullptr);
+    if (deal_roots) {
+        // deal d's roots: pools[deal_roots[d] .. deal_roots[d+1]), their score slots from the
+        // global score offsets (score_offs[i] .. score_offs[i+1] for pool i)
+        b->root_pools.resize((size_t)n_deals);
+        b->root_soff.resize((size_t)n_deals);
+        b->root_scores.resize((size_t)n_deals);
+        for (int64_t d = 0; d < n_deals; d++) {
+            const int64_t a = deal_roots[d], e = deal_roots[d + 1];
+            if (e < a) {
+                delete b;
+                return set_err(ctx, PASUR_EINVAL, "pasur_batch_create_roots: deal_roots must not decrease");
+            }
+            b->root_pools[(size_t)d].assign(pools + a, pools + e);
+            b->root_soff[(size_t)d].assign(1, 0);
+            for (int64_t i = a; i < e; i++) {
+                if (score_offs[i + 1] < score_offs[i]) {
+                    delete b;
+                    return set_err(ctx, PASUR_EINVAL, "pasur_batch_create_roots: score_offs must not decrease");
+                }
+                for (int64_t x = score_offs[i]; x < score_offs[i + 1]; x++) b->root_scores[(size_t)d].push_back(scores[x]);
+                b->root_soff[(size_t)d].push_back((int64_t)b->root_scores[(size_t)d].size());
+            }
+        }
+    }
     int rc = PASUR_OK;
     const bool verbose = getenv("PASUR_VERBOSE") != nullptr;
     using clk = std::chrono::steady_clock;

@@ -142,3 +142,103 @@ extern "C" int pasur_root_values(pasur_tree *t, int mode, const float *sigma, co
     for (auto &x : tmp) dev_free(ctx, x.first, x.second);
     return rc;
 }
+
+namespace pasur {
+namespace {
+
+// reach of the FGT nodes of level k+1 from those of level k: both players following sigma
+__global__ void k_reach_level(int64_t m, const int64_t *__restrict__ child_off, const int64_t *__restrict__ fgt_off,
+                              const int64_t *__restrict__ fgt_off_next, const float *__restrict__ sigma_next,
+                              const double *__restrict__ rin, double *__restrict__ rout) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cb = child_off[j], ce = child_off[j + 1];
+        const int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0;
+        for (int64_t c = cb; c < ce; c++)
+            for (int64_t s = 0; s < ns; s++) {
+                const int64_t q = fgt_off_next[c] + s;
+                rout[q] = __dmul_rn(rin[q0 + s], (double)sigma_next[q]);
+            }
+    }
+}
+
+// every FGT leaf's reach added to its next-round root
+__global__ void k_reach_next(int64_t n, const int64_t *__restrict__ lnk, const double *__restrict__ r, double *next) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        if (r[q] != 0.0) atomicAdd(&next[lnk[q]], r[q]);
+}
+
+}  // namespace
+}  // namespace pasur
+
+extern "C" int pasur_round_reach(pasur_tree *t, const float *sigma, const double *root_reach, double *next_reach,
+                                 int64_t cap) {
+    if (!t) return PASUR_EINVAL;
+    pasur_ctx *ctx = t->ctx;
+    if (!t->unfolded || t->final_round || !t->has_next)
+        return set_err(ctx, PASUR_EINVAL, "pasur_round_reach: needs an unfolded non-final tree after pasur_next_roots");
+    if (!sigma && !t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_round_reach: no strategy (no CFR run, sigma NULL)");
+    if (!next_reach || cap < t->n_next_roots)
+        return set_err(ctx, PASUR_EOVERFLOW, "pasur_round_reach: need " + std::to_string(t->n_next_roots) + " doubles");
+    cudaSetDevice(ctx->device);
+    std::vector<std::pair<void *, size_t>> tmp;
+    int rc = PASUR_OK;
+    auto al = [&](void **p, size_t b) {
+        if (rc != PASUR_OK) return;
+        rc = dev_alloc(ctx, p, b);
+        if (rc == PASUR_OK) tmp.push_back({*p, b});
+    };
+    int64_t ne = 0, base[9] = {0};
+    for (int k = 1; k < 9; k++) {
+        base[k] = ne;
+        ne += t->Q[k];
+    }
+    const float *sg = nullptr;
+    if (sigma && is_device_ptr(sigma)) {
+        sg = sigma;
+    } else {
+        float *d = nullptr;
+        al((void **)&d, sizeof(float) * (size_t)(ne + 1));
+        if (rc == PASUR_OK) {
+            if (sigma) rc = cudaMemcpyAsync(d, sigma, sizeof(float) * (size_t)ne, cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess ? PASUR_OK : set_err(ctx, PASUR_ECUDA, "copy sigma");
+            else rc = cfr_export_sigma(t, d);
+        }
+        sg = d;
+    }
+    double *r[9] = {nullptr}, *nx = nullptr;
+    for (int k = 0; k < 9; k++) al((void **)&r[k], sizeof(double) * (size_t)(t->Q[k] + 1));
+    al((void **)&nx, sizeof(double) * (size_t)(t->n_next_roots + 1));
+    if (rc == PASUR_OK) {
+        std::vector<double> ones;
+        const double *src = root_reach;
+        if (!root_reach) {
+            ones.assign((size_t)t->Q[0], 1.0);
+            src = ones.data();
+        }
+        if (t->Q[0] > 0 && cudaMemcpyAsync(r[0], src, sizeof(double) * (size_t)t->Q[0],
+                                           is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                           ctx->stream) != cudaSuccess)
+            rc = set_err(ctx, PASUR_ECUDA, "copy root reach");
+        if (rc == PASUR_OK && cudaMemsetAsync(nx, 0, sizeof(double) * (size_t)(t->n_next_roots + 1), ctx->stream) != cudaSuccess)
+            rc = set_err(ctx, PASUR_ECUDA, "memset");
+        if (rc == PASUR_OK && !root_reach) rc = cudaStreamSynchronize(ctx->stream) == cudaSuccess ? PASUR_OK : set_err(ctx, PASUR_ECUDA, "sync");
+    }
+    for (int k = 0; k < 8 && rc == PASUR_OK; k++) {
+        if (t->M[k] == 0) continue;
+        k_reach_level<<<grid_of(t->M[k]), 256, 0, ctx->stream>>>(t->M[k], t->child_off[k], t->fgt_off[k], t->fgt_off[k + 1],
+                                                                 sg + base[k + 1], r[k], r[k + 1]);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_reach_level launch");
+    }
+    if (rc == PASUR_OK && t->Q[8] > 0) {
+        k_reach_next<<<grid_of(t->Q[8]), 256, 0, ctx->stream>>>(t->Q[8], t->lnk_d, r[8], nx);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_reach_next launch");
+    }
+    if (rc == PASUR_OK && t->n_next_roots > 0 &&
+        cudaMemcpyAsync(next_reach, nx, sizeof(double) * (size_t)t->n_next_roots,
+                        is_device_ptr(next_reach) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        rc = set_err(ctx, PASUR_ECUDA, "copy next reach");
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PASUR_OK) rc = set_err(ctx, PASUR_ECUDA, "pasur_round_reach: sync");
+    for (auto &x : tmp) dev_free(ctx, x.first, x.second);
+    return rc;
+}

@@ -34,7 +34,8 @@ EXPORTS = [
     "pasur_mlp_dataset_size", "pasur_mlp_dataset_export", "pasur_mlp_dataset_clear", "pasur_mlp_train",
     "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
-    "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes",
+    "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes", "pasur_round_reach",
+    "pasur_batch_create_roots", "pasur_batch_set_cut_values",
 ]
 
 
@@ -93,6 +94,9 @@ def load() -> C.CDLL:
     L.pasur_root_paths.argtypes = [vp, vp, i64]
     L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
     L.pasur_root_sizes.argtypes = [vp, vp, i64]
+    L.pasur_round_reach.argtypes = [vp, vp, vp, vp, i64]
+    L.pasur_batch_create_roots.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp, vp, C.POINTER(pasur_config), C.POINTER(vp)]
+    L.pasur_batch_set_cut_values.argtypes = [vp, i64, vp, i64]
     L.pasur_cfr_convergence.argtypes = [vp, C.POINTER(pasur_config), vp, vp, C.c_int, vp]
     L.pasur_move_offsets_noalloc.argtypes = [vp, i64, vp, vp]
     L.pasur_batch_create.argtypes = [vp, vp, i64, C.c_int, C.POINTER(pasur_config), C.POINTER(vp)]
@@ -388,10 +392,29 @@ def chain_values(trees, mode: int, sigmas=None) -> np.ndarray:
 class Batch:
     """pasur_batch_create / _solve / _tree / _stats / _free: many deals solved together."""
 
-    def __init__(self, ctx: Ctx, decks, first_round: int, cfg: pasur_config, last_round: int = 5, mlp=None):
+    def __init__(self, ctx: Ctx, decks, first_round: int, cfg: pasur_config, last_round: int = 5, mlp=None, roots=None):
+        """roots: None, or per deal (pools, score offsets, scores) of its first round
+        (pasur_batch_create_roots)."""
         d = np.ascontiguousarray(np.asarray(decks, np.uint8).reshape(-1, 52))
         h = vp()
-        if last_round == 5 and mlp is None:
+        if roots is not None:
+            dr, pl, so, sc = [0], [], [0], []
+            for pools, soff, scores in roots:
+                pools = np.asarray(pools, np.uint64)
+                soff = np.asarray(soff, np.int64)
+                scores = np.asarray(scores, np.int16).reshape(-1, 4)
+                pl.append(pools)
+                base = so[-1]
+                so.extend((base + soff[1:]).tolist())
+                sc.append(scores)
+                dr.append(dr[-1] + len(pools))
+            dr = np.array(dr, np.int64)
+            pl = np.ascontiguousarray(np.concatenate(pl) if pl else np.zeros(0, np.uint64), np.uint64)
+            so = np.array(so, np.int64)
+            sc = np.ascontiguousarray(np.concatenate(sc) if sc else np.zeros((0, 4), np.int16), np.int16)
+            rc = load().pasur_batch_create_roots(ctx.h, _ptr(d), d.shape[0], first_round, _ptr(dr), _ptr(pl), _ptr(so),
+                                                 _ptr(sc), C.byref(cfg), C.byref(h))
+        elif last_round == 5 and mlp is None:
             rc = load().pasur_batch_create(ctx.h, _ptr(d), d.shape[0], first_round, C.byref(cfg), C.byref(h))
         else:
             rc = load().pasur_batch_create_cut(ctx.h, _ptr(d), d.shape[0], first_round, last_round, C.byref(cfg),
@@ -427,6 +450,11 @@ class Batch:
         ms, e, l = C.c_float(0), C.c_int64(0), C.c_int64(0)
         _check(load().pasur_batch_stats(self.h, C.byref(ms), C.byref(e), C.byref(l)), self.ctx.h)
         return ms.value, e.value, l.value
+
+    def pasur_batch_set_cut_values(self, deal: int, values):
+        v = values if hasattr(values, "data_ptr") else np.ascontiguousarray(values, np.float32)
+        n = v.numel() if hasattr(v, "numel") else len(v)
+        _check(load().pasur_batch_set_cut_values(self.h, deal, _ptr(v), n), self.ctx.h)
 
     def pasur_batch_work(self):
         """(FGT edges over the solved slots, swept edges with CFR state) of one solve."""
@@ -516,6 +544,14 @@ class Tree:
         if next_root_util is not None:
             nu = next_root_util if hasattr(next_root_util, "data_ptr") else np.ascontiguousarray(next_root_util, np.float32)
         self._c(load().pasur_cfr_iterate_roots(self.h, C.byref(cfg), _ptr(nu), root_first, root_count))
+
+    def pasur_round_reach(self, root_reach=None, sigma=None) -> np.ndarray:
+        """Probability of every next-round root when both follow sigma (default: own sigma-bar)."""
+        out = np.zeros(max(self.n_next_roots(), 1), np.float64)
+        rr = None if root_reach is None else np.ascontiguousarray(root_reach, np.float64)
+        sg = None if sigma is None else (sigma if hasattr(sigma, "data_ptr") else np.ascontiguousarray(sigma, np.float32))
+        self._c(load().pasur_round_reach(self.h, _ptr(sg), _ptr(rr), _ptr(out), self.n_next_roots()))
+        return out[:self.n_next_roots()]
 
     def pasur_root_sizes(self) -> np.ndarray:
         n = int(self.pasur_tree_sizes()[0][0])

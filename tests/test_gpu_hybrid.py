@@ -1,0 +1,143 @@
+"""The pieces of the surrogate's exact fallback (paper_2508_06559_gb300/hybrid.py).
+
+- pasur_round_reach: the probability of every next-round root under the average strategies
+  conserves probability (each round's roots pass on exactly their own reach) and equals the same
+  product of strategies along every path computed from the oracle's tree structure;
+- pasur_batch_create_roots: a batch started from a subset of a round's roots gives those roots
+  the utilities of the batch over all roots, bit for bit (roots are independent);
+- pasur_batch_set_cut_values: a cut batch given the exact next-round utilities reproduces the
+  exact batch's early rounds bit for bit;
+- the fallback loop runs and, solving every reached root exactly, ends with an exploitability no
+  worse than the surrogate alone.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SEEDS = [1, 4, 7]
+T = 60
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2508_06559_gb300 import build as B
+    from paper_2508_06559_gb300 import pasur
+    B.build()
+    return pasur
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.Ctx(0)
+    yield c
+    c.close()
+
+
+def test_round_reach(P, ctx):
+    deck = P.pasur_deal(9)
+    pools = np.array([sum(1 << int(c) for c in deck[:4])], np.uint64)
+    t3 = ctx.pasur_build_round(deck, 3, pools)
+    t3.unfold_single()
+    p4, s4, c4, _ = t3.pasur_next_roots()
+    t4 = ctx.pasur_build_round(deck, 4, p4)
+    t4.pasur_unfold(s4, c4)
+    t4.pasur_next_roots()
+    t3.pasur_cfr_iterate(P.pasur_config_default(iters=T), np.zeros(len(c4), np.float32))
+    t4.pasur_cfr_iterate(P.pasur_config_default(iters=T), np.zeros(t4.n_next_roots(), np.float32))
+    r4 = t3.pasur_round_reach()
+    r5 = t4.pasur_round_reach(root_reach=r4)
+    # probability is conserved up to the float32 normalisation of the average strategies (each
+    # parent's strategies sum to 1 within a few float32 ulps, over 8 levels per round)
+    assert abs(r4.sum() - 1.0) < 1e-6 and abs(r5.sum() - 1.0) < 2e-6 and (r5 >= 0).all()
+    # the same product along every path, from the oracle's structure and the GPU's strategies
+    ot = O.Tree(deck, 3, pools)
+    ot.unfold_single()
+    sb = np.asarray(t3.pasur_avg_strategy(), np.float64)
+    q = ot.sizes()[1]
+    reach, base = np.ones(int(q[0])), 0
+    for k in range(1, 9):
+        reach = reach[ot.fgt_parents(k)] * sb[base:base + q[k]]
+        base += int(q[k])
+    _, _, _, lnk = ot.next_roots()
+    want = np.bincount(lnk, weights=reach, minlength=len(c4))
+    assert np.allclose(r4, want, rtol=1e-12, atol=1e-15)
+    for t in (t3, t4):
+        t.free()
+
+
+def test_batch_from_roots_and_cut_values(P, ctx):
+    decks = np.stack([P.pasur_deal(s) for s in SEEDS])
+    cfg = P.pasur_config_default(iters=T, threads=128)
+    full = P.Batch(ctx, decks, 0, cfg)
+    full.pasur_batch_solve()
+    # a batch of rounds 4-6 from every other root of round 4 of each deal
+    roots, picked = [], []
+    for d in range(len(SEEDS)):
+        pools, soff, scores, _ = full.pasur_batch_tree(d, 2).pasur_next_roots()
+        sel = np.arange(0, len(scores), 2)
+        root_of = np.repeat(np.arange(len(pools)), np.diff(soff))
+        g = root_of[sel]
+        up = np.unique(g)
+        so = np.concatenate([[0], np.cumsum([(g == p).sum() for p in up])]).astype(np.int64)
+        roots.append((pools[up], so, scores[sel]))
+        picked.append(sel)
+    sub = P.Batch(ctx, decks, 3, cfg, roots=roots)
+    sub.pasur_batch_solve()
+    for d in range(len(SEEDS)):
+        u_full = np.asarray(full.pasur_batch_tree(d, 3).pasur_round_utilities())
+        u_sub = np.asarray(sub.pasur_batch_tree(d, 3).pasur_round_utilities())
+        assert np.array_equal(u_sub, u_full[picked[d]])
+    sub.free()
+    # a cut batch (rounds 1-3) given the exact round-4 utilities: the exact early rounds
+    net = P.Mlp(ctx, seed=3)
+    cut = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
+    for d in range(len(SEEDS)):
+        cut.pasur_batch_set_cut_values(d, full.pasur_batch_tree(d, 3).pasur_round_utilities())
+    with pytest.raises(P.PasurError):
+        cut.pasur_batch_set_cut_values(0, np.zeros(3, np.float32))
+    cut.pasur_batch_solve()
+    for d in range(len(SEEDS)):
+        for r in range(3):
+            a, b = cut.pasur_batch_tree(d, r), full.pasur_batch_tree(d, r)
+            assert np.array_equal(a.pasur_round_utilities(), b.pasur_round_utilities())
+            assert np.array_equal(a.pasur_avg_strategy(), b.pasur_avg_strategy())
+    cut.free()
+    net.free()
+    full.free()
+
+
+def test_fallback_loop(P, ctx):
+    import torch
+
+    from paper_2508_06559_gb300 import hybrid as H
+    decks = np.stack([P.pasur_deal(s) for s in SEEDS])
+    cfg = P.pasur_config_default(iters=T, threads=128)
+    full = P.Batch(ctx, decks, 0, cfg)
+    full.pasur_batch_solve()
+    te = [[full.pasur_batch_tree(d, r) for r in range(6)] for d in range(len(SEEDS))]
+    net = P.Mlp(ctx, seed=3)
+
+    def expl(b):
+        out = []
+        for d in range(len(SEEDS)):
+            sig = [b.pasur_batch_tree(d, r).pasur_avg_strategy() for r in range(3)] + [None] * 3
+            out.append((P.chain_values(te[d], 1, sig)[0] - P.chain_values(te[d], 2, sig)[0]) / 2)
+        return np.array(out)
+
+    alone = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
+    alone.pasur_batch_solve()
+    e_alone = expl(alone)
+    alone.free()
+    b, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=0.0, max_passes=8, torch=torch)
+    e_hyb = expl(b)
+    print("exploitability: surrogate alone", e_alone, "with every reached root exact", e_hyb, st)
+    assert st["exact_roots"] > 0 and st["exact_roots_added"][-1] == 0
+    assert e_hyb.mean() <= e_alone.mean() + 1e-9
+    b.free()
+    net.free()
+    full.free()
