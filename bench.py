@@ -50,6 +50,12 @@ BATCH_DEALS = 64
 METRIC = "CFR node-updates/sec"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 ALG_BYTES_PER_UPDATE = 16   # regret and strategy sum, f32, read + write, per node-update
+# shared-memory bytes the CFR kernel moves per iteration, counted from its node code (one slot):
+# per swept edge the child's regret (read twice, written once), value and strategy sum (read,
+# written) and reach (written), 7 words = 28 B; per (active node, slot) pair its two packed entry
+# words in each pass, its parent's reach in each pass, its own reach and value, 8 words = 32 B
+SMEM_BYTES_PER_EDGE, SMEM_BYTES_PER_PAIR = 28, 32
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks of 4 bytes
 CPU_SAMPLE_SECONDS = 12.0
 # the first seed (counting from 0) whose complete six-round full game tree has over 1e9 nodes, the
 # paper's average deal size: 3.38e9 FGT nodes (seed 0 has 3.4e7)
@@ -122,6 +128,7 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
         solved, swept = t.pasur_solved_sizes()
         _WORK["solved"] = _WORK.get("solved", 0) + int(solved[1:].sum()) * T
         _WORK["swept"] = _WORK.get("swept", 0) + swept * T
+        _WORK["pairs"] = _WORK.get("pairs", 0) + t.pasur_swept_pairs() * T
         q0 = int(t.pasur_tree_sizes()[1][0])
         if out_device:
             U = torch.empty(q0, dtype=torch.float32, device="cuda")
@@ -158,7 +165,7 @@ def solve_batch(P, ctx, decks, first_round: int, T: int, out_device: bool, torch
     u = b.pasur_batch_solve()
     ms, edges, launches = b.pasur_batch_stats()
     solved, swept = b.pasur_batch_work()
-    _WORK.update(solved=solved * T, swept=swept * T)
+    _WORK.update(solved=solved * T, swept=swept * T, pairs=b.pasur_batch_pairs() * T)
     d2h = 0
     info = []
     _BATCH_SIZES[:] = [0] * len(decks)
@@ -307,7 +314,7 @@ def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, t
     b, st = H.solve_hybrid(P, ctx, decks, cfg, _SUR["mlp"], 0, 2, eps=HYBRID_EPS, torch=torch)
     ms, edges, _ = b.pasur_batch_stats()
     solved, swept = b.pasur_batch_work()
-    _WORK.update(solved=solved * T, swept=swept * T)
+    _WORK.update(solved=solved * T, swept=swept * T, pairs=b.pasur_batch_pairs() * T)
     d2h = 0
     info = []
     for d in range(len(decks)):
@@ -407,21 +414,52 @@ def job_rate(total_updates: float, slowest_seconds: float) -> float:
     return total_updates / slowest_seconds
 
 
-def recorded_traffic(workload: str, seed: int):
-    """DRAM bytes of the CFR kernel per step from the committed ncu record, when the workload is
-    the recorded one and the kernel source is unchanged since the capture; else None."""
+def _record(name: str):
+    """A committed ncu summary under profiles/ (JSON), or None when it is missing or the kernel
+    sources it names have changed since the capture (their sha256 differs)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_cfr_items_full_game_seed0.traffic.json")
-    if workload != "full_game" or seed != 0 or not os.path.exists(path):
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256()
     for f in rec["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != rec["source_sha256"]:
+    return rec if h.hexdigest() == rec["source_sha256"] else None
+
+
+def recorded_traffic(workload: str, seed: int):
+    """DRAM bytes of the CFR kernels (every k_cfr_items and k_cfr_cluster launch of one solve) per
+    step from the committed ncu record of this workload, while the kernel source is unchanged
+    since the capture; else None."""
+    rec = _record(f"cfr_{workload}_seed{seed}.traffic.json")
+    if rec is None:
         return None
     return rec["dram_bytes_read_per_solve"] + rec["dram_bytes_write_per_solve"]
+
+
+def onchip_roofline(swept: int, pairs: int, kernel_ms: float, sm_mhz: float, n_sms: int):
+    """The CFR kernel against its on-chip bound: the shared-memory bytes its node code moves (counted
+    per swept edge and per (active node, slot) pair) per second of CFR-kernel time, against the
+    shared-memory bandwidth of every SM at the SM clock measured during the run (32 banks x 4 B per
+    clock), plus the issue and shared-memory counters of the committed ncu record while the source
+    is unchanged."""
+    if not pairs or not kernel_ms:
+        return None
+    moved = SMEM_BYTES_PER_EDGE * swept + SMEM_BYTES_PER_PAIR * pairs
+    ach = moved / (kernel_ms / 1e3) / 1e9
+    peak = SMEM_BYTES_PER_CLK_PER_SM * n_sms * sm_mhz * 1e6 / 1e9
+    out = {"bound": "smem", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "bytes_per_step": moved,
+           "note": (f"{SMEM_BYTES_PER_EDGE} B per swept edge + {SMEM_BYTES_PER_PAIR} B per (active node, slot) "
+                    f"pair per iteration, from the node code; peak = {SMEM_BYTES_PER_CLK_PER_SM} B/clk x {n_sms} SMs "
+                    "x median SM clock of the timed region (derived, not measured)")}
+    rec = _record("cfr_onchip_full_game_seed0.json")
+    if rec is not None:
+        out["ncu"] = {k: rec[k] for k in ("workload", "issue_active_pct", "smem_wavefront_pct_of_peak",
+                                          "bank_conflict_share", "warps_active_pct") if k in rec}
+    return out
 
 
 def measured_peaks():
@@ -466,6 +504,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     ctx = P.Ctx(dev, 0, stream.cuda_stream)
+    ctx_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     first_round, desc = WORKLOADS[args.workload]
     seeds = rank_deal_seeds(args.workload, args.seed, rank)
     T = args.iters
@@ -543,6 +582,9 @@ def run_ours(args, rank, world, dist):
     # carries CFR state, per iteration (the swept node-updates)
     ach_gbs = ALG_BYTES_PER_UPDATE * swept / (kernel_ms / 1e3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    clocks = clk.summary()
+    onchip = onchip_roofline(swept, work[-1].get("pairs", 0), kernel_ms,
+                             float(clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)), ctx_sms)
     line = {
         "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -563,17 +605,19 @@ def run_ours(args, rank, world, dist):
                           "are resolved once")},
         "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ach_gbs / hbm_peak,
                      "traffic": recorded_traffic(args.workload, args.seed),
-                     "traffic_unit": "bytes per step (all k_cfr_items launches of one solve; ncu record in profiles/)",
+                     "traffic_unit": "bytes per step (every k_cfr_items and k_cfr_cluster launch of one solve; ncu "
+                                     "record in profiles/)",
                      "note": (f"k_cfr_items; achieved = {ALG_BYTES_PER_UPDATE} B per swept node-update (R and S "
                               f"read + write) x swept node-updates / CFR kernel time, peak = {src} HBM copy "
                               "bandwidth; the kernel keeps each root's state in shared memory for all T "
                               "iterations, so its DRAM traffic is far below the algorithmic bytes (ncu counters "
                               "in profiles/): the fraction is an HBM-equivalent rate, the kernel is bound on chip "
-                              "(shared memory, issue, block barriers)")},
+                              "(shared memory, issue, block barriers): see onchip")},
+        "onchip": onchip,
         "e2e": {"value": job_rate(job_updates, e2e_mean / 1e3), "unit": "node-updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(1, args.steps),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "root_utility": root_u,
         "selfplay": None if sp is None else dict(
             sp, note="games per deal through every solved round, moves drawn from the average "
@@ -728,11 +772,13 @@ def main():
     ap.add_argument("--no-merge", action="store_true", help="solve every score slot (pasur_config.merge_delta = 0)")
     ap.add_argument("--stream-bytes", type=int, default=0,
                     help="pasur_config.stream_bytes: roots needing more state stream over every SM (0 = default rule)")
+    ap.add_argument("--split-bytes", type=int, default=0,
+                    help="pasur_config.split_bytes: roots needing more state split over a cluster (0 = default rule)")
     args = ap.parse_args()
     if args.seed is None:
         args.seed = FULL_GAME_SEED if args.workload == "full_game" else 0
     SOLVER.update(slots_per_item=args.slots_per_item, threads=args.threads, merge_delta=0 if args.no_merge else 1,
-                  stream_bytes=args.stream_bytes)
+                  stream_bytes=args.stream_bytes, split_bytes=args.split_bytes)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -225,6 +225,13 @@ int pasur_cfr_convergence(pasur_tree *tree, const pasur_config *cfg, const float
  * edge lies on a forced-move chain (average strategy 1, regret 0, never touched per iteration). */
 int pasur_solved_sizes(const pasur_tree *tree, int64_t solved_sizes[9], int64_t *swept_edges);
 
+/* The (active node, solved slot) pairs the CFR updates per iteration (after the first
+ * pasur_cfr_iterate; host out): one regret-matching step in the top-down pass and one value, regret
+ * and strategy-sum update in the bottom-up pass each.  With pasur_solved_sizes' swept edges this is
+ * the kernel's work per iteration (its shared-memory traffic is about 28 B per swept edge plus 32 B
+ * per pair).  EINVAL: NULL out, no CFR run yet. */
+int pasur_swept_pairs(const pasur_tree *tree, int64_t *swept_pairs);
+
 /* How the CFR solves each GT root (after the first pasur_cfr_iterate; host out, cap >= GT roots):
  * 0..4 = one thread block per item with the state in shared memory (size classes, smallest
  * first), 5 = the level-streaming sweep over every SM with the state in device memory, 6 = a
@@ -293,6 +300,9 @@ int pasur_batch_stats(const pasur_batch *b, float *ms, int64_t *edges, int64_t *
 /* The work of one pasur_batch_solve, summed over all trees as in pasur_solved_sizes: FGT edges over
  * the solved slots, and the swept (node, solved slot) pairs that carry CFR state. */
 int pasur_batch_work(const pasur_batch *b, int64_t *solved_edges, int64_t *swept_edges);
+/* The (active node, solved slot) pairs of one pasur_batch_solve iteration, summed over all trees
+ * as in pasur_swept_pairs.  EINVAL: NULL batch or out. */
+int pasur_batch_pairs(const pasur_batch *b, int64_t *swept_pairs);
 int pasur_batch_free(pasur_batch *b);
 
 /* ---- self-play (fair value) ---------------------------------------------------------------- */

@@ -634,6 +634,13 @@ int pasur_solved_sizes(const pasur_tree *t, int64_t solved_sizes[9], int64_t *sw
     return PASUR_OK;
 }
 
+int pasur_swept_pairs(const pasur_tree *t, int64_t *swept_pairs) {
+    if (check_tree(t) || !swept_pairs) return PASUR_EINVAL;
+    if (!t->cfr_ready) return set_err(t->ctx, PASUR_EINVAL, "pasur_swept_pairs: no CFR run yet");
+    *swept_pairs = t->swept_pairs;
+    return PASUR_OK;
+}
+
 int pasur_last_cfr_stats(const pasur_tree *t, float *ms, int64_t *edges, int32_t *launches) {
     if (check_tree(t)) return PASUR_EINVAL;
     if (ms) *ms = t->last_ms;

@@ -36,7 +36,7 @@ struct pasur_batch {
     size_t dcfr_bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int64_t graph_launches = 0, edges = 0, solved_edges = 0, swept_edges = 0;
+    int64_t graph_launches = 0, edges = 0, solved_edges = 0, swept_edges = 0, swept_pairs = 0;
     float last_ms = 0.f;
     bool solved = false;
 };
@@ -70,7 +70,7 @@ struct DealPlan {
     std::vector<CfrItem> own[6][8];
     size_t need[6][8] = {};
     std::vector<ClusterItem> clu[6];
-    int64_t edges = 0, solved_edges = 0, swept_edges = 0;
+    int64_t edges = 0, solved_edges = 0, swept_edges = 0, swept_pairs = 0;
 };
 
 // One deal on the context wc: its rounds forward from the standalone convention root (pool
@@ -127,6 +127,7 @@ int build_deal(pasur_batch *b, pasur_ctx *wc, const uint8_t *deck, int64_t d, De
             o.solved_edges += t->cQ[k];
         }
         o.swept_edges += t->swept_edges;
+        o.swept_pairs += t->swept_pairs;
     }
     PASUR_CUDA(wc, cudaStreamSynchronize(wc->stream));
     return PASUR_OK;
@@ -505,6 +506,7 @@ static int batch_create(pasur_ctx *ctx, const uint8_t *decks, int64_t n_deals, i
         b->edges += o.edges;
         b->solved_edges += o.solved_edges;
         b->swept_edges += o.swept_edges;
+        b->swept_pairs += o.swept_pairs;
     }
     lap(tp, 2);
     if (rc == PASUR_OK) rc = cfr_dcfr_factors(ctx, cfg, 0, &b->dcfr, &b->dcfr_bytes);
@@ -604,6 +606,12 @@ int pasur_batch_work(const pasur_batch *b, int64_t *solved_edges, int64_t *swept
     if (!b) return PASUR_EINVAL;
     if (solved_edges) *solved_edges = b->solved_edges;
     if (swept_edges) *swept_edges = b->swept_edges;
+    return PASUR_OK;
+}
+
+int pasur_batch_pairs(const pasur_batch *b, int64_t *swept_pairs) {
+    if (!b || !swept_pairs) return PASUR_EINVAL;
+    *swept_pairs = b->swept_pairs;
     return PASUR_OK;
 }
 

@@ -91,6 +91,21 @@ __device__ __forceinline__ float tree_sum(const float *x) {
 // number, since counted regrets exceed the dead zone).
 __device__ __forceinline__ float rcp_pos(float s) { return __fdividef(1.f, s); }
 
+// Regret matching over the regrets r of D > 1 child edges: the children's reaches own * sigma.
+template <int D>
+__device__ __forceinline__ void rm_reach(const float *r, float own, float thr, float *x) {
+    float rp[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) rp[a] = r[a] > thr ? r[a] : 0.f;
+    const float sum = tree_sum<D>(rp);
+    const bool pos = sum > 0.f;
+    // pos: rp * scale (an fma with a zero addend rounds the product alone); otherwise every rp is
+    // zero and the fma gives the uniform share: one instruction per child instead of two
+    const float scale = pos ? own * rcp_pos(sum) : 0.f, u = pos ? 0.f : own * (1.f / (float)D);
+#pragma unroll
+    for (int a = 0; a < D; a++) x[a] = __fmaf_rn(rp[a], scale, u);
+}
+
 // Regret matching at one (active node, slot) with D children and the reach of the children.
 // X[n] holds the reach of the player who moved into node n; own = the mover's reach at the node.
 template <int D, bool W1>
@@ -99,20 +114,14 @@ __device__ __forceinline__ void td_node(int c, int sh, int w, float own, const f
     if constexpr (D == 1) {
         X[at<W1>(c, 0, sh, w)] = own;
         return;
-    }
-    float rp[D];
+    } else {
+        float r[D], x[D];
 #pragma unroll
-    for (int a = 0; a < D; a++) {
-        const float r = R[at<W1>(c, a, sh, w)];
-        rp[a] = r > thr ? r : 0.f;
-    }
-    const float sum = tree_sum<D>(rp);
-    const bool pos = sum > 0.f;
-    // pos: rp * scale (an fma with a zero addend rounds the product alone); otherwise every rp is
-    // zero and the fma gives the uniform share: one instruction per child instead of two
-    const float scale = pos ? own * rcp_pos(sum) : 0.f, u = pos ? 0.f : own * (1.f / (float)D);
+        for (int a = 0; a < D; a++) r[a] = R[at<W1>(c, a, sh, w)];
+        rm_reach<D>(r, own, thr, x);
 #pragma unroll
-    for (int a = 0; a < D; a++) X[at<W1>(c, a, sh, w)] = __fmaf_rn(rp[a], scale, u);
+        for (int a = 0; a < D; a++) X[at<W1>(c, a, sh, w)] = x[a];
+    }
 }
 
 template <bool W1>
@@ -135,19 +144,15 @@ __device__ __forceinline__ void td_node_any(int c, int d, int sh, int w, float o
     }
 }
 
-// Value of one (active node, slot) with D children, then R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h))
-// and S(h,a) += pi_p(h) sigma(h,a) for its child edges.  Returns v(h).
-template <int VARIANT, int D, bool W1>
-__device__ __forceinline__ float bu_node(int c, int sh, int w, float pp, float spo, float *__restrict__ R,
-                                         float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
+// Value of a node from the regrets r, strategy sums s and values v of its D child edges, then
+// R(h,a) += s_p pi_{-p}(h) (v(h.a) - v(h)) and S(h,a) += pi_p(h) sigma(h,a) in place in r and s.
+// Returns v(h).
+template <int VARIANT, int D>
+__device__ __forceinline__ float bu_vals(float *r, const float *v, float *s, float pp, float spo, float thr, float fpos,
                                          float fneg, float fs) {
-    float r[D], v[D], rp[D];
+    float rp[D];
 #pragma unroll
-    for (int a = 0; a < D; a++) {
-        r[a] = R[at<W1>(c, a, sh, w)];
-        v[a] = V[at<W1>(c, a, sh, w)];
-        rp[a] = r[a] > thr ? r[a] : 0.f;
-    }
+    for (int a = 0; a < D; a++) rp[a] = r[a] > thr ? r[a] : 0.f;
     const float sum = tree_sum<D>(rp);
     const bool pos = sum > 0.f;
     const float inv = pos ? rcp_pos(sum) : 0.f, u = pos ? 0.f : 1.f / (float)D;
@@ -160,15 +165,38 @@ __device__ __forceinline__ float bu_node(int c, int sh, int w, float pp, float s
     const float vh = D == 1 ? v[0] : v[0] + tree_sum<D>(dv);
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        const int q = at<W1>(c, a, sh, w);
         const float inst = spo * (v[a] - vh);
         if (VARIANT == 1) {
-            R[q] = r[a] * (r[a] > 0.f ? fpos : fneg) + inst;
-            S[q] = S[q] * fs + pp * sg[a];
+            r[a] = r[a] * (r[a] > 0.f ? fpos : fneg) + inst;
+            s[a] = s[a] * fs + pp * sg[a];
         } else {
-            R[q] = r[a] + inst;
-            S[q] = S[q] + pp * sg[a];
+            r[a] = r[a] + inst;
+            s[a] = s[a] + pp * sg[a];
         }
+    }
+    return vh;
+}
+
+// Value of one (active node, slot) with D children and the updates of its child edges (bu_vals)
+// in R and S.  Returns v(h).
+template <int VARIANT, int D, bool W1>
+__device__ __forceinline__ float bu_node(int c, int sh, int w, float pp, float spo, float *__restrict__ R,
+                                         float *__restrict__ S, const float *__restrict__ V, float thr, float fpos,
+                                         float fneg, float fs) {
+    float r[D], v[D], s[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const int q = at<W1>(c, a, sh, w);
+        r[a] = R[q];
+        v[a] = V[q];
+        s[a] = S[q];
+    }
+    const float vh = bu_vals<VARIANT, D>(r, v, s, pp, spo, thr, fpos, fneg, fs);
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const int q = at<W1>(c, a, sh, w);
+        R[q] = r[a];
+        S[q] = s[a];
     }
     return vh;
 }
@@ -749,8 +777,8 @@ __device__ __forceinline__ void store_region(const TreeView &tv, const CfrRoot &
     }
 }
 
-template <int VARIANT>
-__global__ void __launch_bounds__(1024, 1) k_cfr_cluster(CfrParams p, const ClusterItem *__restrict__ clu) {
+template <int VARIANT, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_cluster(CfrParams p, const ClusterItem *__restrict__ clu) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_as[10], t_as[10];
     __shared__ int32_t s_sb[15], s_sn[15], s_sf[15], t_sb[15], t_sn[15], t_sf[15];
@@ -850,6 +878,13 @@ __global__ void __launch_bounds__(1024, 1) k_cfr_cluster(CfrParams p, const Clus
     }
     cl_sync();  // no CTA leaves while another may still address its shared memory
 }
+
+// The cluster kernel for blocks of `threads` threads: up to 256 at up to 80 registers (no spills;
+// room for class blocks beside a cluster's block on an SM), beyond that at up to 64 (a
+// 1024-thread block on one SM).
+const void *const kClusterKernels[4] = {(const void *)k_cfr_cluster<0, 256>, (const void *)k_cfr_cluster<1, 256>,
+                                        (const void *)k_cfr_cluster<0, 1024>, (const void *)k_cfr_cluster<1, 1024>};
+const void *cluster_kernel_for(int variant, int threads) { return kClusterKernels[(threads > 256 ? 2 : 0) + (variant == 1)]; }
 
 struct LevelPtrs {
     const int64_t *fgt[9];
@@ -1632,11 +1667,14 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     }
     t->data_size = data;
     t->scratch_size = scratch;
-    t->swept_edges = 0;
+    t->swept_edges = t->swept_pairs = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         const CfrRoot &cr = t->croots_h[(size_t)g];
-        if (cr.ls[9] > 1 && t->in_range(g))
-            t->swept_edges += (int64_t)(cr.ls[9] - 1) * (t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g]);
+        if (cr.ls[9] > 1 && t->in_range(g)) {
+            const int64_t ns = t->csoff_h[(size_t)g + 1] - t->csoff_h[(size_t)g];
+            t->swept_edges += (int64_t)(cr.ls[9] - 1) * ns;
+            t->swept_pairs += (int64_t)cr.as[9] * ns;
+        }
     }
     if (!splits.empty()) {
         // append the parts' entries and local leaf indices; pseudo-roots after the real roots
@@ -1862,8 +1900,12 @@ int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float 
 int ensure_aux(pasur_ctx *ctx) {
     if (ctx->fork) return PASUR_OK;
     PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    int least = 0, greatest = 0;
+    PASUR_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     for (int c = 0; c < kClsCluster + kCluGroups; c++) {
-        PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking));
+        // the level-streaming sweep is a chain of short dependent launches: its blocks go first
+        // whenever an SM frees up, the persistent classes and the clusters fill the rest
+        PASUR_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->aux[c], cudaStreamNonBlocking, c == kClsGlobal ? greatest : least));
         PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming));
         PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t0[c]));
         PASUR_CUDA(ctx, cudaEventCreate(&ctx->cls_t1[c]));
@@ -1914,20 +1956,15 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
     p.err = ctx->errflag;
     PASUR_CUDA(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int32_t) * kNumCls, ctx->stream));
     PASUR_CUDA(ctx, cudaEventRecord(ctx->fork, ctx->stream));
-    // the classes are independent: each runs on its own forked stream, largest subtrees first
+    // the classes are independent: each runs on its own forked stream, largest subtrees first; the
+    // level-streaming sweep (thousands of short launches) is queued last, after every persistent
+    // class and cluster launch, so that the host never waits on its queue before the others start
     for (int oi = 0; oi < kNumCls; oi++) {
         const int c = kNumCls - 1 - oi;
-        if (plan.cls_end[c] == plan.cls_begin[c]) continue;
+        if (plan.cls_end[c] == plan.cls_begin[c] || c == kClsGlobal) continue;
         cudaStream_t st = ctx->aux[c];
         PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
         PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[c], st));
-        if (c == kClsGlobal) {
-            PASUR_TRY(stream_sweep(ctx, plan, p, cfg, st));
-            PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
-            PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
-            PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
-            continue;
-        }
         p.i_begin = plan.cls_begin[c];
         p.i_end = plan.cls_end[c];
         p.counter = ctx->counter + c;
@@ -1961,12 +1998,21 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
         lc.attrs = at;
         lc.numAttrs = 1;
         const ClusterItem *ci = plan.clu_d + plan.clu_begin[b];
-        if (cfg->variant == 1) PASUR_CUDA(ctx, cudaLaunchKernelEx(&lc, k_cfr_cluster<1>, p, ci));
-        else PASUR_CUDA(ctx, cudaLaunchKernelEx(&lc, k_cfr_cluster<0>, p, ci));
+        void *args[] = {&p, &ci};
+        PASUR_CUDA(ctx, cudaLaunchKernelExC(&lc, cluster_kernel_for(cfg->variant, plan.clu_threads), args));
         ctx->launches++;
         PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));
         PASUR_CUDA(ctx, cudaEventRecord(ctx->join[c], st));
         PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[c], 0));
+    }
+    if (plan.cls_end[kClsGlobal] != plan.cls_begin[kClsGlobal]) {
+        cudaStream_t st = ctx->aux[kClsGlobal];
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fork, 0));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t0[kClsGlobal], st));
+        PASUR_TRY(stream_sweep(ctx, plan, p, cfg, st));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[kClsGlobal], st));
+        PASUR_CUDA(ctx, cudaEventRecord(ctx->join[kClsGlobal], st));
+        PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join[kClsGlobal], 0));
     }
     return PASUR_OK;
 }
@@ -1976,20 +2022,18 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
 int cfr_cluster_smem_limit(pasur_ctx *ctx, size_t *limit) {
     size_t st = 0;
     cudaFuncAttributes fa;
-    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_cluster<0>));
-    st = std::max(st, fa.sharedSizeBytes);
-    PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k_cfr_cluster<1>));
-    st = std::max(st, fa.sharedSizeBytes);
+    for (const void *k : kClusterKernels) {
+        PASUR_CUDA(ctx, cudaFuncGetAttributes(&fa, k));
+        st = std::max(st, fa.sharedSizeBytes);
+    }
     *limit = ctx->smem_optin > st ? ctx->smem_optin - st : 0;
     return PASUR_OK;
 }
 
 int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg) {
-    (void)cfg;
     size_t lim = 0;
     PASUR_TRY(cfr_cluster_smem_limit(ctx, &lim));
-    const void *ks[2] = {(const void *)k_cfr_cluster<0>, (const void *)k_cfr_cluster<1>};
-    for (const void *k : ks) {
+    for (const void *k : kClusterKernels) {
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
         PASUR_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
@@ -2008,7 +2052,7 @@ int cfr_cluster_check(pasur_ctx *ctx, CfrPlan *plan, const pasur_config *cfg) {
         lc.attrs = at;
         lc.numAttrs = 1;
         int nclusters = 0;
-        PASUR_CUDA(ctx, cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_cfr_cluster<0>, &lc));
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveClusters(&nclusters, cluster_kernel_for(cfg->variant, plan->clu_threads), &lc));
         if (nclusters < 1)
             return set_err(ctx, PASUR_EINVAL, "a cluster of " + std::to_string(plan->clu_ctas[b]) + " blocks of " +
                                                   std::to_string(plan->clu_smem[b]) + " B shared memory cannot be resident");

@@ -299,6 +299,7 @@ struct pasur_tree {
     int64_t *cfgt_off[9] = {nullptr};   // per GT node: first solved FGT node (= fgt_off unless merged)
     int64_t cQ[9] = {0};                // solved FGT level sizes
     int64_t swept_edges = 0;            // (local non-root node, solved slot) pairs: edges with CFR state
+    int64_t swept_pairs = 0;            // (active node, solved slot) pairs: node updates per iteration
     // next round links
     bool has_next = false;
     int64_t *lnk_d = nullptr;           // Q[8]

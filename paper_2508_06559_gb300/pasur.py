@@ -35,7 +35,7 @@ EXPORTS = [
     "pasur_mlp_predict_next", "pasur_mlp_root_features", "pasur_mlp_stats", "pasur_root_values",
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
     "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes", "pasur_round_reach",
-    "pasur_batch_create_roots", "pasur_batch_set_cut_values",
+    "pasur_batch_create_roots", "pasur_batch_set_cut_values", "pasur_swept_pairs", "pasur_batch_pairs",
 ]
 
 
@@ -91,6 +91,8 @@ def load() -> C.CDLL:
     L.pasur_last_cfr_stats.argtypes = [vp, C.POINTER(C.c_float), i64p, C.POINTER(C.c_int32)]
     L.pasur_solved_sizes.argtypes = [vp, vp, i64p]
     L.pasur_batch_work.argtypes = [vp, i64p, i64p]
+    L.pasur_swept_pairs.argtypes = [vp, i64p]
+    L.pasur_batch_pairs.argtypes = [vp, i64p]
     L.pasur_root_paths.argtypes = [vp, vp, i64]
     L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
     L.pasur_root_sizes.argtypes = [vp, vp, i64]
@@ -462,6 +464,12 @@ class Batch:
         _check(load().pasur_batch_work(self.h, C.byref(a), C.byref(b)), self.ctx.h)
         return a.value, b.value
 
+    def pasur_batch_pairs(self) -> int:
+        """(active node, solved slot) pairs updated per iteration, all trees."""
+        a = C.c_int64(0)
+        _check(load().pasur_batch_pairs(self.h, C.byref(a)), self.ctx.h)
+        return a.value
+
     def pasur_batch_selfplay(self, n_games: int, seeds, out=None):
         """n_games games per deal (deal d under seeds[d]); int16 [n_deals, n_games]."""
         sd = np.ascontiguousarray(seeds, np.uint64)
@@ -521,6 +529,12 @@ class Tree:
         e = C.c_int64(0)
         self._c(load().pasur_solved_sizes(self.h, _ptr(c), C.byref(e)))
         return c, e.value
+
+    def pasur_swept_pairs(self) -> int:
+        """(active node, solved slot) pairs updated per iteration, after the first pasur_cfr_iterate."""
+        e = C.c_int64(0)
+        self._c(load().pasur_swept_pairs(self.h, C.byref(e)))
+        return e.value
 
     def pasur_unfold(self, score_offs, scores) -> np.ndarray:
         so = np.ascontiguousarray(score_offs, np.int64)
