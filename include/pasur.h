@@ -101,7 +101,9 @@ int pasur_config_default(pasur_config *cfg);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no limit beyond the
  * device's memory.  cuda_stream is a cudaStream_t (NULL = a new non-blocking stream owned by
- * the context). */
+ * the context).  The context's device memory comes from its own stream-ordered pool: memory a
+ * freed tree or batch held stays reserved for the context's next allocations (no new mappings
+ * per solve) and returns to the device at pasur_destroy; the budget counts live allocations. */
 int pasur_create(pasur_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
 /* Release the context.  EINVAL (and nothing is released) while trees of the context are alive. */
 int pasur_destroy(pasur_ctx *ctx);

@@ -34,13 +34,13 @@ int dev_alloc(pasur_ctx *ctx, void **p, size_t bytes) {
         a->in_use += bytes;
         a->peak = std::max(a->peak, a->in_use);
     }
-    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, a->pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         std::lock_guard<std::mutex> lk(a->acct_mu);
         a->in_use -= std::min(a->in_use, bytes);
-        return set_err(ctx, PASUR_ENOMEM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return set_err(ctx, PASUR_ENOMEM, std::string("cudaMallocFromPoolAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
     return PASUR_OK;
 }
@@ -181,8 +181,19 @@ int pasur_create(pasur_ctx **out, int device, size_t hbm_budget_bytes, void *cud
             ctx->own_stream = true;
         }
     }
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&ctx->pool, &props);
+        uint64_t keep = UINT64_MAX;  // never trim at synchronisation: reuse instead of remapping
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     if (e != cudaSuccess) {
         std::string m = std::string("pasur_create: ") + cudaGetErrorString(e);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return set_err(nullptr, PASUR_ECUDA, m);
     }
@@ -192,6 +203,8 @@ int pasur_create(pasur_ctx **out, int device, size_t hbm_budget_bytes, void *cud
     if (rc == PASUR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = PASUR_ECUDA;
     if (rc != PASUR_OK) {
         std::string m = ctx->err;
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return set_err(nullptr, rc, "pasur_create: " + m);
@@ -217,6 +230,7 @@ int pasur_destroy(pasur_ctx *ctx) {
         if (ctx->cls_t1[c]) cudaEventDestroy(ctx->cls_t1[c]);
     }
     if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PASUR_OK;
@@ -424,11 +438,15 @@ int pasur_cfr_iterate(pasur_tree *t, const pasur_config *cfg, const float *next_
                                                 cudaMemcpyHostToDevice, ctx->stream));
             }
         }
+        PhaseTimer pt(ctx->stream, "cfr set-up");
         int rc = plan_solve_slots(t, cfg->merge_delta != 0, nu);
+        pt.mark("solved slots");
         if (rc == PASUR_OK) rc = compute_leaf_values(t, nu);
+        pt.mark("leaf values");
         if (nb) dev_free(ctx, nu, nb);
         if (rc != PASUR_OK) return rc;
         PASUR_TRY(cfr_prepare(t, cfg));
+        pt.mark("layout and plan");
     }
     t->variant = cfg->variant;
     return cfr_run(t, cfg);

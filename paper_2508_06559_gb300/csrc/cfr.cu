@@ -20,10 +20,13 @@
 // of each level are numbered in the order of their parents' entries, so the children of
 // consecutive entries are consecutive.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <string>
+#include <thread>
 
 #include "pasur_internal.cuh"
 
@@ -1342,6 +1345,7 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
         if (need > dyn_max || (cfg->split_bytes > 0 && need > (size_t)cfg->split_bytes)) cand.push_back(g);
     }
     if (cand.empty()) return PASUR_OK;
+    PhaseTimer pt(ctx->stream, "cluster splits");
     // host copies of the layout
     const int64_t NA = t->n_active, NL = t->n_local;
     std::vector<int32_t> hli((size_t)NA), hpl((size_t)NA), hcs((size_t)NA);
@@ -1353,8 +1357,21 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
     PASUR_CUDA(ctx, cudaMemcpy(hd.data(), t->act_d, sizeof(uint16_t) * (size_t)NA, cudaMemcpyDeviceToHost));
     PASUR_CUDA(ctx, cudaMemcpy(hgt.data(), t->act_gt, sizeof(int64_t) * (size_t)NA, cudaMemcpyDeviceToHost));
     PASUR_CUDA(ctx, cudaMemcpy(htq.data(), t->loc_tq, sizeof(int64_t) * (size_t)NL, cudaMemcpyDeviceToHost));
+    pt.mark("host copies");
     const size_t target = cfg->split_bytes > 0 ? std::min<size_t>((size_t)cfg->split_bytes, part_max) : part_max;
-    for (int64_t g : cand) {
+    const bool verbose = getenv("PASUR_VERBOSE") != nullptr;
+    // the split of one root, its pseudo-roots' offsets relative to its own entries and nodes
+    struct RootSplit {
+        bool done = false;
+        SplitRoot sr;
+        CfrRoot top{};
+        std::vector<CfrRoot> parts;
+        std::vector<int32_t> li, pl, cs, cx;
+        std::vector<uint16_t> d;
+        std::vector<int64_t> gt, tq;
+        std::string msg;
+    };
+    auto split_one = [&](int64_t g, RootSplit &o) {
         const CfrRoot cr = t->croots_h[(size_t)g];
         const int64_t L = cr.ls[9], nA = cr.as[9];
         const int32_t *li = hli.data() + cr.act_off, *pl = hpl.data() + cr.act_off, *cs = hcs.data() + cr.act_off;
@@ -1433,16 +1450,13 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
                 SplitRoot sr;
                 sr.ell = ell;
                 sr.nparts = np;
-                sr.top_root = (int32_t)t->croots_h.size();
-                sr.part_root0 = sr.top_root + 1;
-                sr.x0 = (int64_t)t->cx_h.size() / 5;
                 sr.top_L = cr.ls[ell + 1];
                 CfrRoot top = cr;
                 for (int k = ell + 1; k < 10; k++) top.as[k] = cr.as[ell];
                 for (int k = ell + 2; k < 10; k++) top.ls[k] = cr.ls[ell + 1];
                 top.W = 1;
                 top.cls = kClsCluster;
-                t->croots_h.push_back(top);
+                o.top = top;
                 std::vector<int32_t> part_of_sub((size_t)ns);
                 for (int q = 0; q < np; q++)
                     for (int i = first[(size_t)q]; i < first[(size_t)q + 1]; i++) part_of_sub[(size_t)i] = q;
@@ -1461,14 +1475,14 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
                     }
                     for (int i = first[(size_t)q]; i < first[(size_t)q + 1]; i++) ghost[(size_t)heads[(size_t)i]] = (int32_t)n++;
                     pr.ls[9] = (int32_t)n;
-                    pr.loc_off = (int64_t)(NL + ntq.size());
-                    pr.act_off = (int64_t)(NA + nli.size());
+                    pr.loc_off = (int64_t)o.tq.size();  // relative: placed after the other roots' parts when merged
+                    pr.act_off = (int64_t)o.li.size();
                     std::vector<int64_t> tq((size_t)n, -1);
                     for (int64_t x = cr.ls[ell]; x < L; x++) {
                         const int32_t sid = sub[(size_t)x];
                         if (sid >= 0 && part_of_sub[(size_t)sid] == q) tq[(size_t)newidx[(size_t)x]] = htq[(size_t)(cr.loc_off + x)];
                     }
-                    ntq.insert(ntq.end(), tq.begin(), tq.end());
+                    o.tq.insert(o.tq.end(), tq.begin(), tq.end());
                     int32_t m = 0;
                     for (int k = 0; k <= ell; k++) pr.as[k] = 0;
                     for (int k = ell; k < 8; k++) {
@@ -1476,18 +1490,18 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
                         for (int32_t e = cr.as[k]; e < cr.as[k + 1]; e++) {
                             const int32_t sid = sub[(size_t)li[e]];
                             if (sid < 0 || part_of_sub[(size_t)sid] != q) continue;
-                            nli.push_back(newidx[(size_t)li[e]]);
-                            npl.push_back(k == ell ? ghost[(size_t)li[e]] : newidx[(size_t)pl[e]]);
-                            ncs.push_back(newidx[(size_t)cs[e]]);
-                            nd.push_back(dd[e]);
-                            ngt.push_back(hgt[(size_t)(cr.act_off + e)]);
+                            o.li.push_back(newidx[(size_t)li[e]]);
+                            o.pl.push_back(k == ell ? ghost[(size_t)li[e]] : newidx[(size_t)pl[e]]);
+                            o.cs.push_back(newidx[(size_t)cs[e]]);
+                            o.d.push_back(dd[e]);
+                            o.gt.push_back(hgt[(size_t)(cr.act_off + e)]);
                             m++;
                         }
                     }
                     pr.as[8] = pr.as[9] = m;
                     pr.W = 1;
                     pr.cls = kClsCluster;
-                    t->croots_h.push_back(pr);
+                    o.parts.push_back(pr);
                     sr.part_L.push_back(n);
                     size_t b = resident_bytes(n, m, 1);
                     if (q == 0) b += resident_bytes(sr.top_L, cr.as[ell], 1);
@@ -1497,27 +1511,92 @@ int plan_splits(pasur_tree *t, const pasur_config *cfg, size_t dyn_max, size_t p
                 for (size_t i = 0; i < heads.size(); i++) {
                     const int32_t x = heads[i];
                     const int32_t e = ent_of[(size_t)x];
-                    t->cx_h.push_back(part_of_sub[i]);
-                    t->cx_h.push_back(x);
-                    t->cx_h.push_back(pl[e]);
-                    t->cx_h.push_back(newidx[(size_t)x]);
-                    t->cx_h.push_back(ghost[(size_t)x]);
+                    o.cx.push_back(part_of_sub[i]);
+                    o.cx.push_back(x);
+                    o.cx.push_back(pl[e]);
+                    o.cx.push_back(newidx[(size_t)x]);
+                    o.cx.push_back(ghost[(size_t)x]);
                 }
                 sr.nx = (int32_t)heads.size();
                 sr.smem = smax;
-                split_of[(size_t)g] = (int32_t)splits.size();
-                splits.push_back(sr);
-                done = true;
+                o.sr = std::move(sr);
+                o.done = done = true;
             }
-            if (!done && getenv("PASUR_VERBOSE")) {
+            if (!done && verbose) {
                 int64_t big = 0;
                 for (int i = 0; i < ns; i++) big = std::max<int64_t>(big, (int64_t)resident_bytes(sl[(size_t)i] + 1, sa[(size_t)i], 1));
-                fprintf(stderr, "[pasur] root %lld (L %lld, active %lld): no split at level %d: %d subtrees, top %zu B, "
-                                "largest subtree %lld B, part limit %zu B\n",
-                        (long long)g, (long long)L, (long long)nA, ell, ns, top_bytes, (long long)big, part_max);
+                char line[256];
+                snprintf(line, sizeof line, "[pasur] root %lld (L %lld, active %lld): no split at level %d: %d subtrees, top %zu B, "
+                                            "largest subtree %lld B, part limit %zu B\n",
+                         (long long)g, (long long)L, (long long)nA, ell, ns, top_bytes, (long long)big, part_max);
+                o.msg += line;
             }
         }
+    };
+    // roots are independent: split them on host threads, then append the results in root order
+    std::vector<RootSplit> res(cand.size());
+    std::atomic<size_t> next{0};
+    std::atomic<bool> failed{false};
+    auto worker = [&]() {
+        try {
+            for (size_t i = next++; i < cand.size(); i = next++) split_one(cand[i], res[i]);
+        } catch (...) {
+            failed = true;
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nw = std::min<size_t>({(size_t)hw, (size_t)16, cand.size()});
+    auto run_workers = [&](const std::function<void()> &fn) {
+        std::vector<std::thread> th;
+        for (size_t w = 1; w < nw; w++) th.emplace_back(fn);
+        fn();
+        for (auto &x : th) x.join();
+    };
+    run_workers(worker);
+    if (failed) return set_err(ctx, PASUR_ENOMEM, "cluster split: host allocation failed");
+    pt.mark("per-root splits");
+    // root order: pseudo-roots, exchange entries and the offsets of every root's entries and nodes
+    std::vector<size_t> a_at(cand.size() + 1, nli.size()), l_at(cand.size() + 1, ntq.size());
+    for (size_t ci = 0; ci < cand.size(); ci++) {
+        RootSplit &o = res[ci];
+        if (!o.msg.empty()) fputs(o.msg.c_str(), stderr);
+        a_at[ci + 1] = a_at[ci] + o.li.size();
+        l_at[ci + 1] = l_at[ci] + o.tq.size();
+        if (!o.done) continue;
+        SplitRoot sr = std::move(o.sr);
+        sr.top_root = (int32_t)t->croots_h.size();
+        sr.part_root0 = sr.top_root + 1;
+        sr.x0 = (int64_t)t->cx_h.size() / 5;
+        t->croots_h.push_back(o.top);
+        for (CfrRoot pr : o.parts) {
+            pr.loc_off += NL + (int64_t)l_at[ci];
+            pr.act_off += NA + (int64_t)a_at[ci];
+            t->croots_h.push_back(pr);
+        }
+        t->cx_h.insert(t->cx_h.end(), o.cx.begin(), o.cx.end());
+        split_of[(size_t)cand[ci]] = (int32_t)splits.size();
+        splits.push_back(std::move(sr));
     }
+    // the entries and node links, copied into place by the host threads
+    nli.resize(a_at.back());
+    npl.resize(a_at.back());
+    ncs.resize(a_at.back());
+    nd.resize(a_at.back());
+    ngt.resize(a_at.back());
+    ntq.resize(l_at.back());
+    next = 0;
+    run_workers([&]() {
+        for (size_t ci = next++; ci < cand.size(); ci = next++) {
+            const RootSplit &o = res[ci];
+            std::copy(o.li.begin(), o.li.end(), nli.begin() + (ptrdiff_t)a_at[ci]);
+            std::copy(o.pl.begin(), o.pl.end(), npl.begin() + (ptrdiff_t)a_at[ci]);
+            std::copy(o.cs.begin(), o.cs.end(), ncs.begin() + (ptrdiff_t)a_at[ci]);
+            std::copy(o.d.begin(), o.d.end(), nd.begin() + (ptrdiff_t)a_at[ci]);
+            std::copy(o.gt.begin(), o.gt.end(), ngt.begin() + (ptrdiff_t)a_at[ci]);
+            std::copy(o.tq.begin(), o.tq.end(), ntq.begin() + (ptrdiff_t)l_at[ci]);
+        }
+    });
+    pt.mark("merge");
     return PASUR_OK;
 }
 
@@ -1549,7 +1628,9 @@ int cfr_cluster_smem_limit(pasur_ctx *ctx, size_t *limit);
 int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector<CfrItem> *cls_items, size_t *need,
                    std::vector<ClusterItem> *clu) {
     pasur_ctx *ctx = t->ctx;
+    PhaseTimer pt(ctx->stream, "cfr plan");
     PASUR_TRY(build_layout(t));
+    pt.mark("layout");
     // every root goes to the smallest shared-memory class its subtree fits with one slot; its
     // items then take as many slots as that class holds
     size_t dyn_max = 0;
@@ -1582,6 +1663,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     PASUR_TRY(cfr_cluster_smem_limit(ctx, &dyn_cl));
     PASUR_TRY(plan_splits(t, cfg, dyn_max, std::min(dyn_max, dyn_cl), streamed, splits, split_of, nli, npl, ncs, nd, ngt,
                           ntq));
+    pt.mark("cluster splits");
     int64_t data = 0, scratch = 0;
     for (int64_t g = 0; g < t->n_roots; g++) {
         CfrRoot &cr = t->croots_h[(size_t)g];
@@ -1745,6 +1827,7 @@ int cfr_setup_tree(pasur_tree *t, const pasur_config *cfg, int tree, std::vector
     v.cx = t->cx_d;
     t->iters_done = 0;
     t->cfr_ready = true;
+    pt.mark("items and state");
     return PASUR_OK;
 }
 

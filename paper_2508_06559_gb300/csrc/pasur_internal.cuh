@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -119,6 +122,10 @@ struct pasur_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the context's stream-ordered memory pool: freed blocks stay reserved for the next
+    // allocation (a solve's arrays are reused by the next solve without new mappings) until
+    // pasur_destroy returns them
+    cudaMemPool_t pool = nullptr;
     size_t budget = 0, in_use = 0, peak = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
@@ -142,6 +149,28 @@ struct pasur_ctx {
     // allocations are charged to (and limited by the budget of) the parent context
     pasur_ctx *acct = nullptr;
     std::mutex acct_mu;
+};
+
+// Host phases of a call under PASUR_VERBOSE: each mark waits for the context's stream and prints
+// the wall time since the previous mark (a diagnostic; without the variable it does nothing).
+struct PhaseTimer {
+    cudaStream_t stream;
+    const char *what;
+    bool on;
+    std::chrono::steady_clock::time_point t0;
+    PhaseTimer(cudaStream_t s, const char *w) : stream(s), what(w), on(getenv("PASUR_VERBOSE") != nullptr) {
+        if (on) {
+            cudaStreamSynchronize(stream);
+            t0 = std::chrono::steady_clock::now();
+        }
+    }
+    void mark(const char *phase) {
+        if (!on) return;
+        cudaStreamSynchronize(stream);
+        const auto t1 = std::chrono::steady_clock::now();
+        fprintf(stderr, "[pasur] %s: %s %.2f ms\n", what, phase, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        t0 = t1;
+    }
 };
 
 struct RootInfo {             // one GT root's subtree, level by level
