@@ -227,6 +227,20 @@ int pasur_cfr_convergence(pasur_tree *tree, const pasur_config *cfg, const float
  * edge lies on a forced-move chain (average strategy 1, regret 0, never touched per iteration). */
 int pasur_solved_sizes(const pasur_tree *tree, int64_t solved_sizes[9], int64_t *swept_edges);
 
+/* Checkpoint and resume of a round's CFR (the paper keeps each round's state in host memory and
+ * stores solved profiles, section "Experimental Evaluation").  After the tree's CFR has been set
+ * up (its first pasur_cfr_iterate; iters 0 allowed), pasur_save_round writes the round's regrets,
+ * strategy sums, root-value sums, iteration count and variant, after a header of sizes and a hash
+ * of its leaf values, into buf (host memory, cap bytes); with buf NULL it only sets *bytes to the
+ * size it needs.  pasur_load_round restores such a checkpoint into a tree built, unfolded and set
+ * up the same way (same deal, round, roots, score slots, next-round utilities, variant and solver
+ * settings): the next pasur_cfr_iterate continues the saved run as if it had not stopped, bit for
+ * bit.  buf: host memory, read or written only during the call.  Errors: EINVAL (no CFR set-up,
+ * cap too small, not a checkpoint, truncated, or a header or leaf hash that differs from the
+ * tree's), ECUDA. */
+int pasur_save_round(const pasur_tree *tree, void *buf, size_t cap, size_t *bytes);
+int pasur_load_round(pasur_tree *tree, const void *buf, size_t bytes);
+
 /* The (active node, solved slot) pairs the CFR updates per iteration (after the first
  * pasur_cfr_iterate; host out): one regret-matching step in the top-down pass and one value, regret
  * and strategy-sum update in the bottom-up pass each.  With pasur_solved_sizes' swept edges this is

@@ -43,10 +43,10 @@ constexpr int kClsGlobal = kNumCls - 1;
 constexpr int kClsCluster = 6;       // plan class of the cluster items' pseudo-items (exports only)
 constexpr int kMaxClusterCtas = 16;  // CTAs of a cluster (16: non-portable size)
 // default block size per class (the batch autotuner measures its own); class 3 at two 256-thread
-// blocks per SM measured faster than one 512-thread block of the 512-thread instantiation, and
-// class 4 (one block per SM) faster at 256 than at 1024 threads (fewer warps idle at the level
-// barriers: seed-47 final round 306 -> 293 ms)
-constexpr int kClsThreads[kNumCls] = {128, 128, 256, 256, 256, 1024};
+// blocks per SM measured faster than one 512-thread block of the 512-thread instantiation; class 4
+// (one block per SM) at 512 threads: more warps to cover the level steps' latency than at 256
+// (seed-47 CFR 1234 -> 1175 ms) and fewer idle at the barriers than at 1024
+constexpr int kClsThreads[kNumCls] = {128, 128, 256, 256, 512, 1024};
 
 struct CfrParams {
     const CfrItem *items;
@@ -882,12 +882,14 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_cluster(CfrPa
     cl_sync();  // no CTA leaves while another may still address its shared memory
 }
 
-// The cluster kernel for blocks of `threads` threads: up to 256 at up to 80 registers (no spills;
-// room for class blocks beside a cluster's block on an SM), beyond that at up to 64 (a
-// 1024-thread block on one SM).
-const void *const kClusterKernels[4] = {(const void *)k_cfr_cluster<0, 256>, (const void *)k_cfr_cluster<1, 256>,
+// The cluster kernel for blocks of `threads` threads: up to 256 at up to 80 registers, up to 512 at
+// up to 128 (no spills), beyond that at up to 64 (a 1024-thread block on one SM).
+const void *const kClusterKernels[6] = {(const void *)k_cfr_cluster<0, 256>,  (const void *)k_cfr_cluster<1, 256>,
+                                        (const void *)k_cfr_cluster<0, 512>,  (const void *)k_cfr_cluster<1, 512>,
                                         (const void *)k_cfr_cluster<0, 1024>, (const void *)k_cfr_cluster<1, 1024>};
-const void *cluster_kernel_for(int variant, int threads) { return kClusterKernels[(threads > 256 ? 2 : 0) + (variant == 1)]; }
+const void *cluster_kernel_for(int variant, int threads) {
+    return kClusterKernels[(threads > 512 ? 4 : threads > 256 ? 2 : 0) + (variant == 1)];
+}
 
 struct LevelPtrs {
     const int64_t *fgt[9];
@@ -1867,9 +1869,9 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         }
         plan.clu_end[b] = i;
     }
-    // one block width for the cluster launches: 256 threads (a part's level steps are short;
-    // on the seed-47 final round 256 threads measured faster than 1024: 1096 -> 1071 ms)
-    plan.clu_threads = 256;
+    // one block width for the cluster launches: 512 threads, one CTA per SM (seed-47 CFR with class
+    // 4 at 512: 1175 -> 1110 ms; 1024 threads measured slower than 256)
+    plan.clu_threads = 512;
     if (cfg->threads > 0) plan.clu_threads = cfg->threads;
     if (!plan.clu_h.empty()) {
         size_t b = sizeof(ClusterItem) * plan.clu_h.size();

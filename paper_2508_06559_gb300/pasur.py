@@ -36,6 +36,7 @@ EXPORTS = [
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
     "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes", "pasur_round_reach",
     "pasur_batch_create_roots", "pasur_batch_set_cut_values", "pasur_swept_pairs", "pasur_batch_pairs",
+    "pasur_save_round", "pasur_load_round",
 ]
 
 
@@ -92,6 +93,8 @@ def load() -> C.CDLL:
     L.pasur_solved_sizes.argtypes = [vp, vp, i64p]
     L.pasur_batch_work.argtypes = [vp, i64p, i64p]
     L.pasur_swept_pairs.argtypes = [vp, i64p]
+    L.pasur_save_round.argtypes = [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pasur_load_round.argtypes = [vp, vp, C.c_size_t]
     L.pasur_batch_pairs.argtypes = [vp, i64p]
     L.pasur_root_paths.argtypes = [vp, vp, i64]
     L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
@@ -529,6 +532,18 @@ class Tree:
         e = C.c_int64(0)
         self._c(load().pasur_solved_sizes(self.h, _ptr(c), C.byref(e)))
         return c, e.value
+
+    def pasur_save_round(self) -> np.ndarray:
+        """The round's CFR checkpoint (header, regrets, strategy sums, root-value sums) as bytes."""
+        n = C.c_size_t(0)
+        self._c(load().pasur_save_round(self.h, None, 0, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        self._c(load().pasur_save_round(self.h, _ptr(buf), n.value, C.byref(n)))
+        return buf
+
+    def pasur_load_round(self, buf) -> None:
+        b = np.ascontiguousarray(buf, np.uint8)
+        self._c(load().pasur_load_round(self.h, _ptr(b), b.nbytes))
 
     def pasur_swept_pairs(self) -> int:
         """(active node, solved slot) pairs updated per iteration, after the first pasur_cfr_iterate."""
