@@ -139,7 +139,8 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
             d2h += U.nbytes + sb.nbytes
         t.pasur_round_utilities(U)
         if edges:
-            t.pasur_avg_strategy(sb)
+            # the strategies travel to the host while the next round solves (pasur_sync below)
+            t.pasur_avg_strategy_async(sb)
         outs.append(sb)
         nxt = U
     root_u = float(nxt[0]) if len(nxt) else 0.0
@@ -150,6 +151,7 @@ def solve_deal(P, ctx, deck, first_round: int, T: int, out_device: bool, torch):
         games = host_out(torch, "games", SELFPLAY_GAMES, np.int16)
         d2h += games.nbytes
     ctx.pasur_selfplay(trees, SELFPLAY_GAMES, int(deck_seed(deck)), sigmas=None, out=games)
+    ctx.pasur_sync()
     sp = selfplay_summary(ctx, games)
     info = [(t.pasur_tree_sizes()[1].tolist()) for t in trees]
     for t in trees:

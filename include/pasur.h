@@ -184,6 +184,16 @@ int pasur_avg_strategy(const pasur_tree *tree, float *out, int64_t cap);
  * of iterations; CodeSnippet "CFR").  out: float, host or device, cap >= FGT level-0 size. */
 int pasur_round_utilities(const pasur_tree *tree, float *out, int64_t cap);
 
+/* pasur_avg_strategy without waiting: the strategies are computed on the context's stream and,
+ * for host memory, copied to out on a copy stream of the context that runs beside the context's
+ * later work (the next round's CFR); for device memory the call is ordered on the context's
+ * stream.  out must stay valid and unread until pasur_sync(ctx) returns; a host buffer should be
+ * page-locked for the copy to overlap.  Same layout and errors as pasur_avg_strategy. */
+int pasur_avg_strategy_async(const pasur_tree *tree, float *out, int64_t cap);
+
+/* Wait for everything the context queued: its stream and the copies of asynchronous exports. */
+int pasur_sync(pasur_ctx *ctx);
+
 /* Between-hand update (section "Between-Hand Updates", CodeSnippet "BetweenHands"): the next
  * round's FGT roots.  For every FGT leaf (j, s) the next root is (pool at j, normalise(score s +
  * the round's clubs and point difference at j)).  Roots: unique pools ascending, per pool unique

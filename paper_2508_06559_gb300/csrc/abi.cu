@@ -230,6 +230,11 @@ int pasur_destroy(pasur_ctx *ctx) {
         if (ctx->cls_t1[c]) cudaEventDestroy(ctx->cls_t1[c]);
     }
     if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->copy_after) cudaEventDestroy(ctx->copy_after);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -472,6 +477,47 @@ int pasur_avg_strategy(const pasur_tree *t, float *out, int64_t cap) {
     if (rc == PASUR_OK) rc = copy_out(ctx, out, tmp, ne);
     dev_free(ctx, tmp, b);
     return rc;
+}
+
+int pasur_avg_strategy_async(const pasur_tree *t, float *out, int64_t cap) {
+    if (check_tree(t)) return PASUR_EINVAL;
+    pasur_ctx *ctx = t->ctx;
+    set_device(ctx);
+    if (!t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_avg_strategy_async: no CFR run yet");
+    int64_t ne = 0;
+    for (int k = 1; k < 9; k++) ne += t->Q[k];
+    if (!out || cap < ne) return set_err(ctx, PASUR_EOVERFLOW, "pasur_avg_strategy_async: need " + std::to_string(ne) + " floats");
+    if (is_device_ptr(out)) return cfr_export_sigma(t, out);  // stream-ordered on the context's stream
+    if (!ctx->copy_stream) {
+        PASUR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        PASUR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_after, cudaEventDisableTiming));
+    }
+    float *tmp = nullptr;
+    const size_t b = sizeof(float) * (size_t)(ne + 1);
+    PASUR_TRY(dev_alloc(ctx, (void **)&tmp, b));
+    int rc = cfr_export_sigma(t, tmp);
+    if (rc != PASUR_OK) {
+        dev_free(ctx, tmp, b);
+        return rc;
+    }
+    // the copy and the release of the staging buffer follow the export on the copy stream, so the
+    // context's stream (the next round's CFR) runs on while the strategies travel to the host
+    PASUR_CUDA(ctx, cudaEventRecord(ctx->copy_after, ctx->stream));
+    PASUR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_after, 0));
+    PASUR_CUDA(ctx, cudaMemcpyAsync(out, tmp, sizeof(float) * (size_t)ne, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    PASUR_CUDA(ctx, cudaFreeAsync(tmp, ctx->copy_stream));
+    pasur_ctx *a = ctx->acct ? ctx->acct : ctx;
+    std::lock_guard<std::mutex> lk(a->acct_mu);
+    a->in_use -= std::min(a->in_use, b);
+    return PASUR_OK;
+}
+
+int pasur_sync(pasur_ctx *ctx) {
+    if (!ctx) return PASUR_EINVAL;
+    set_device(ctx);
+    PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->copy_stream) PASUR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
+    return PASUR_OK;
 }
 
 int pasur_round_utilities(const pasur_tree *t, float *out, int64_t cap) {

@@ -126,6 +126,10 @@ struct pasur_ctx {
     // allocation (a solve's arrays are reused by the next solve without new mappings) until
     // pasur_destroy returns them
     cudaMemPool_t pool = nullptr;
+    // device-to-host copies of asynchronous exports (created on first use), after an event on
+    // the context's stream; pasur_sync waits for them
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_after = nullptr;
     size_t budget = 0, in_use = 0, peak = 0;
     int num_sms = 0;
     size_t smem_optin = 0;

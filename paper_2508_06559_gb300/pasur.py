@@ -36,7 +36,7 @@ EXPORTS = [
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
     "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes", "pasur_round_reach",
     "pasur_batch_create_roots", "pasur_batch_set_cut_values", "pasur_swept_pairs", "pasur_batch_pairs",
-    "pasur_save_round", "pasur_load_round",
+    "pasur_save_round", "pasur_load_round", "pasur_avg_strategy_async", "pasur_sync",
 ]
 
 
@@ -95,6 +95,8 @@ def load() -> C.CDLL:
     L.pasur_swept_pairs.argtypes = [vp, i64p]
     L.pasur_save_round.argtypes = [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.pasur_load_round.argtypes = [vp, vp, C.c_size_t]
+    L.pasur_avg_strategy_async.argtypes = [vp, vp, i64]
+    L.pasur_sync.argtypes = [vp]
     L.pasur_batch_pairs.argtypes = [vp, i64p]
     L.pasur_root_paths.argtypes = [vp, vp, i64]
     L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
@@ -230,6 +232,10 @@ class Ctx:
             self.close()
         except Exception:
             pass
+
+    def pasur_sync(self) -> None:
+        """Wait for the context's stream and the copies of asynchronous exports."""
+        _check(load().pasur_sync(self.h), self.h)
 
     def memory(self):
         a, b = C.c_size_t(0), C.c_size_t(0)
@@ -597,6 +603,13 @@ class Tree:
             out = np.zeros(ne, np.float32)
         n = out.numel() if hasattr(out, "numel") else len(out)
         self._c(load().pasur_avg_strategy(self.h, _ptr(out), n))
+        return out
+
+    def pasur_avg_strategy_async(self, out):
+        """pasur_avg_strategy without waiting: out (host, page-locked for overlap, or device) is
+        complete after the context's pasur_sync."""
+        n = out.numel() if hasattr(out, "numel") else len(out)
+        self._c(load().pasur_avg_strategy_async(self.h, _ptr(out), n))
         return out
 
     def pasur_round_utilities(self, out=None):
