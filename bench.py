@@ -44,6 +44,7 @@ WORKLOADS = {
 SUR_DEALS = 64
 HYBRID_EPS = 1e-3       # the timed form's reach threshold
 HYBRID_FRONTIER = (None, 1e-2, 1e-3, 1e-4, 0.0)  # None = the surrogate alone
+HYBRID_RESPONSE_FRONTIER = (1e-2, 1e-3, 1e-4)     # roots reached by best responses too
 SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..), rounds 4-6 from the standalone root
 SUR_LABEL_ITERS = 300
 BATCH_DEALS = 64
@@ -275,9 +276,10 @@ def surrogate_setup(P, ctx, decks, T, torch):
         return ex
 
     frontier = []
-    for eps in HYBRID_FRONTIER:
+    forms = [(eps, "reach") for eps in HYBRID_FRONTIER] + [(eps, "response") for eps in HYBRID_RESPONSE_FRONTIER]
+    for eps, select in forms:
         for key, net in (("surrogate", mlp), ("no_learning", none)):
-            if key == "no_learning" and eps is not None:
+            if key == "no_learning" and (eps is not None or select != "reach"):
                 continue
             torch.cuda.synchronize()
             if eps is None:
@@ -287,11 +289,11 @@ def surrogate_setup(P, ctx, decks, T, torch):
                 torch.cuda.synchronize()
                 st = dict(passes=0, exact_roots=0, wall_s=time.perf_counter() - t2)
             else:
-                bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch)
+                bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch, select=select)
             ex = judge(bs)
             bs.free()
             gap = float(np.mean(ex)) - float(np.mean(expl_exact))
-            frontier.append({"net": key, "eps": eps, "create_solve_s": st["wall_s"],
+            frontier.append({"net": key, "eps": eps, "select": select, "create_solve_s": st["wall_s"],
                              "speedup_vs_exact": exact_s / st["wall_s"], "exploitability_mean": float(np.mean(ex)),
                              "gap_vs_exact": gap, "max_deal_gap": float(np.max(np.array(ex) - np.array(expl_exact))),
                              "passes": st["passes"], "exact_round4_roots": st["exact_roots"],

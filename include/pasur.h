@@ -383,6 +383,16 @@ int pasur_round_reach(pasur_tree *tree, const float *sigma, const double *root_r
  * order (no fused multiply-add).  out: double [FGT roots], host or device. */
 int pasur_root_values(pasur_tree *tree, int mode, const float *sigma, const double *next_values, double *out, int64_t cap);
 
+/* Probability of every next-round root when one player best-responds and the other follows sigma:
+ * mode 1 Alex best-responds, 2 Bob does, 3 both follow sigma (as pasur_round_reach).  The
+ * responder's move at each of its nodes is the choice of the value pass of pasur_root_values with
+ * the same mode, sigma and next_values (the first best child in canonical order); reach is
+ * multiplied in fp64.  root_reach: double per FGT root of this round, host or device (NULL = 1
+ * each); next_values: double per next-round FGT root, host or device (required); next_reach:
+ * double [next roots], host or device.  Non-final rounds after pasur_next_roots only. */
+int pasur_response_reach(pasur_tree *tree, int mode, const float *sigma, const double *next_values,
+                         const double *root_reach, double *next_reach, int64_t cap);
+
 /* ---- round-start utility surrogate ---------------------------------------------------------- */
 /* A 256-256-256-256-1 network (GELU hidden layers) that predicts the average utility U of a
  * round-start FGT root, so that a round's leaves can take their next-round values (eq.

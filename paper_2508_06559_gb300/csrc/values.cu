@@ -66,18 +66,15 @@ unsigned grid_of(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int
 
 using namespace pasur;
 
-extern "C" int pasur_root_values(pasur_tree *t, int mode, const float *sigma, const double *next_values, double *out,
-                                 int64_t cap) {
-    if (!t) return PASUR_EINVAL;
+namespace {
+
+// The shared part of the value and reach passes: the strategy on the device (copied, or the
+// tree's own average strategy when sigma is NULL), the next-round values on the device, and the
+// values of every FGT level under `mode` (v[0..8]; mode 3 = both players on sigma).  Device
+// temporaries are appended to tmp.
+int value_levels(pasur_tree *t, int mode, const float *sigma, const double *next_values,
+                 std::vector<std::pair<void *, size_t>> &tmp, const float **sg_out, double *v[9]) {
     pasur_ctx *ctx = t->ctx;
-    if (mode < 0 || mode > 3) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: mode must be 0..3");
-    if (!t->unfolded) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: tree not unfolded");
-    if (!t->final_round && (!next_values || !t->has_next))
-        return set_err(ctx, PASUR_EINVAL, "pasur_root_values: a non-final round needs pasur_next_roots and next_values");
-    if (mode != 0 && !sigma && !t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: no strategy (no CFR run, sigma NULL)");
-    if (!out || cap < t->Q[0]) return set_err(ctx, PASUR_EOVERFLOW, "pasur_root_values: need " + std::to_string(t->Q[0]) + " doubles");
-    cudaSetDevice(ctx->device);
-    std::vector<std::pair<void *, size_t>> tmp;
     int rc = PASUR_OK;
     auto al = [&](void **p, size_t b) {
         if (rc != PASUR_OK) return;
@@ -118,7 +115,6 @@ extern "C" int pasur_root_values(pasur_tree *t, int mode, const float *sigma, co
             nx = d;
         }
     }
-    double *v[9] = {nullptr};
     for (int k = 0; k < 9; k++) al((void **)&v[k], sizeof(double) * (size_t)(t->Q[k] + 1));
     if (rc == PASUR_OK && t->M[8] > 0) {
         k_leaf_f64<<<grid_of(t->M[8]), 256, 0, ctx->stream>>>(t->st[8], t->root[8], t->M[8], t->fgt_off[8], t->score_off_d,
@@ -134,6 +130,27 @@ extern "C" int pasur_root_values(pasur_tree *t, int mode, const float *sigma, co
         ctx->launches++;
         if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_value_level launch");
     }
+    *sg_out = sg;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int pasur_root_values(pasur_tree *t, int mode, const float *sigma, const double *next_values, double *out,
+                                 int64_t cap) {
+    if (!t) return PASUR_EINVAL;
+    pasur_ctx *ctx = t->ctx;
+    if (mode < 0 || mode > 3) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: mode must be 0..3");
+    if (!t->unfolded) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: tree not unfolded");
+    if (!t->final_round && (!next_values || !t->has_next))
+        return set_err(ctx, PASUR_EINVAL, "pasur_root_values: a non-final round needs pasur_next_roots and next_values");
+    if (mode != 0 && !sigma && !t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_root_values: no strategy (no CFR run, sigma NULL)");
+    if (!out || cap < t->Q[0]) return set_err(ctx, PASUR_EOVERFLOW, "pasur_root_values: need " + std::to_string(t->Q[0]) + " doubles");
+    cudaSetDevice(ctx->device);
+    std::vector<std::pair<void *, size_t>> tmp;
+    const float *sg = nullptr;
+    double *v[9] = {nullptr};
+    int rc = value_levels(t, mode, sigma, next_values, tmp, &sg, v);
     if (rc == PASUR_OK && t->Q[0] > 0 &&
         cudaMemcpyAsync(out, v[0], sizeof(double) * (size_t)t->Q[0], is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         ctx->stream) != cudaSuccess)
@@ -158,6 +175,42 @@ __global__ void k_reach_level(int64_t m, const int64_t *__restrict__ child_off, 
                 const int64_t q = fgt_off_next[c] + s;
                 rout[q] = __dmul_rn(rin[q0 + s], (double)sigma_next[q]);
             }
+    }
+}
+
+// reach of level k+1 from level k when one player best-responds (mode 1: Alex, 2: Bob; values of
+// level k+1 under that mode in vnext): at the responder's nodes the whole reach goes to the child
+// its value pass chose (the first best child in canonical order), at the other player's nodes it
+// follows sigma
+__global__ void k_response_reach_level(int k, int64_t m, int mode, const int64_t *__restrict__ child_off,
+                                       const int64_t *__restrict__ fgt_off, const int64_t *__restrict__ fgt_off_next,
+                                       const float *__restrict__ sigma_next, const double *__restrict__ vnext,
+                                       const double *__restrict__ rin, double *__restrict__ rout) {
+    const bool alex = (k & 1) == 0;
+    const bool responder = (mode == 1 && alex) || (mode == 2 && !alex);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cb = child_off[j], ce = child_off[j + 1];
+        const int64_t q0 = fgt_off[j], ns = fgt_off[j + 1] - q0;
+        for (int64_t s = 0; s < ns; s++) {
+            const double r = rin[q0 + s];
+            if (responder) {
+                int64_t arg = cb;
+                double best = 0.0;
+                for (int64_t c = cb; c < ce; c++) {
+                    const double v = vnext[fgt_off_next[c] + s];
+                    if (c == cb || (alex ? v > best : v < best)) {
+                        best = v;
+                        arg = c;
+                    }
+                }
+                for (int64_t c = cb; c < ce; c++) rout[fgt_off_next[c] + s] = c == arg ? r : 0.0;
+            } else {
+                for (int64_t c = cb; c < ce; c++) {
+                    const int64_t q = fgt_off_next[c] + s;
+                    rout[q] = __dmul_rn(r, (double)sigma_next[q]);
+                }
+            }
+        }
     }
 }
 
@@ -239,6 +292,71 @@ extern "C" int pasur_round_reach(pasur_tree *t, const float *sigma, const double
                         is_device_ptr(next_reach) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         rc = set_err(ctx, PASUR_ECUDA, "copy next reach");
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PASUR_OK) rc = set_err(ctx, PASUR_ECUDA, "pasur_round_reach: sync");
+    for (auto &x : tmp) dev_free(ctx, x.first, x.second);
+    return rc;
+}
+
+extern "C" int pasur_response_reach(pasur_tree *t, int mode, const float *sigma, const double *next_values,
+                                    const double *root_reach, double *next_reach, int64_t cap) {
+    if (!t) return PASUR_EINVAL;
+    pasur_ctx *ctx = t->ctx;
+    if (mode < 1 || mode > 3) return set_err(ctx, PASUR_EINVAL, "pasur_response_reach: mode must be 1..3");
+    if (!t->unfolded || t->final_round || !t->has_next)
+        return set_err(ctx, PASUR_EINVAL, "pasur_response_reach: needs an unfolded non-final tree after pasur_next_roots");
+    if (!next_values) return set_err(ctx, PASUR_EINVAL, "pasur_response_reach: next_values is required");
+    if (!sigma && !t->cfr_ready) return set_err(ctx, PASUR_EINVAL, "pasur_response_reach: no strategy (no CFR run, sigma NULL)");
+    if (!next_reach || cap < t->n_next_roots)
+        return set_err(ctx, PASUR_EOVERFLOW, "pasur_response_reach: need " + std::to_string(t->n_next_roots) + " doubles");
+    cudaSetDevice(ctx->device);
+    std::vector<std::pair<void *, size_t>> tmp;
+    const float *sg = nullptr;
+    double *v[9] = {nullptr};
+    int rc = value_levels(t, mode, sigma, next_values, tmp, &sg, v);
+    auto al = [&](void **p, size_t b) {
+        if (rc != PASUR_OK) return;
+        rc = dev_alloc(ctx, p, b);
+        if (rc == PASUR_OK) tmp.push_back({*p, b});
+    };
+    double *r[9] = {nullptr}, *nx = nullptr;
+    for (int k = 0; k < 9; k++) al((void **)&r[k], sizeof(double) * (size_t)(t->Q[k] + 1));
+    al((void **)&nx, sizeof(double) * (size_t)(t->n_next_roots + 1));
+    std::vector<double> ones;
+    if (rc == PASUR_OK) {
+        const double *src = root_reach;
+        if (!root_reach) {
+            ones.assign((size_t)t->Q[0], 1.0);
+            src = ones.data();
+        }
+        if (t->Q[0] > 0 && cudaMemcpyAsync(r[0], src, sizeof(double) * (size_t)t->Q[0],
+                                           is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                           ctx->stream) != cudaSuccess)
+            rc = set_err(ctx, PASUR_ECUDA, "copy root reach");
+        if (rc == PASUR_OK && cudaMemsetAsync(nx, 0, sizeof(double) * (size_t)(t->n_next_roots + 1), ctx->stream) != cudaSuccess)
+            rc = set_err(ctx, PASUR_ECUDA, "memset");
+    }
+    int64_t base[9] = {0}, ne = 0;
+    for (int k = 1; k < 9; k++) {
+        base[k] = ne;
+        ne += t->Q[k];
+    }
+    for (int k = 0; k < 8 && rc == PASUR_OK; k++) {
+        if (t->M[k] == 0) continue;
+        k_response_reach_level<<<grid_of(t->M[k]), 256, 0, ctx->stream>>>(k, t->M[k], mode, t->child_off[k], t->fgt_off[k],
+                                                                          t->fgt_off[k + 1], sg + base[k + 1], v[k + 1], r[k],
+                                                                          r[k + 1]);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_response_reach_level launch");
+    }
+    if (rc == PASUR_OK && t->Q[8] > 0) {
+        k_reach_next<<<grid_of(t->Q[8]), 256, 0, ctx->stream>>>(t->Q[8], t->lnk_d, r[8], nx);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) rc = set_err(ctx, PASUR_ECUDA, "k_reach_next launch");
+    }
+    if (rc == PASUR_OK && t->n_next_roots > 0 &&
+        cudaMemcpyAsync(next_reach, nx, sizeof(double) * (size_t)t->n_next_roots,
+                        is_device_ptr(next_reach) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        rc = set_err(ctx, PASUR_ECUDA, "copy next reach");
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == PASUR_OK) rc = set_err(ctx, PASUR_ECUDA, "pasur_response_reach: sync");
     for (auto &x : tmp) dev_free(ctx, x.first, x.second);
     return rc;
 }

@@ -8,7 +8,10 @@ after the cut that the current average strategies reach with probability above e
 their exact utilities replace the predictions (pasur_batch_set_cut_values) and the early rounds
 are solved again.  It stops when a pass adds no root, or after max_passes.  With eps = 0 every
 root the play can reach is exact when it stops; larger eps trade exactness off the likely lines
-of play for time.
+of play for time.  With select="response" a root is also chosen when a best response of either
+player to the other's current average strategies (pasur_response_reach, the best responses taken
+on the current after-cut values) reaches it with probability above eps: exploitability is what
+best responses gain, and they go where the average strategies rarely do.
 """
 from __future__ import annotations
 
@@ -25,8 +28,24 @@ def root_reach_after_cut(batch, deal: int, first_round: int, last_round: int):
     return r
 
 
+def response_reach_after_cut(batch, deal: int, first_round: int, last_round: int, cut_values, mode: int):
+    """Probability of every root after the cut when one player best-responds (mode 1 Alex, 2 Bob)
+    to the other's average strategies, the after-cut roots valued at cut_values: best-response
+    values chained backward over the cut rounds, then the reach forward."""
+    trees = [batch.pasur_batch_tree(deal, r) for r in range(first_round, last_round + 1)]
+    nxt_of = [None] * len(trees)
+    nxt = np.asarray(cut_values, np.float64)
+    for i in range(len(trees) - 1, -1, -1):
+        nxt_of[i] = nxt
+        nxt = trees[i].pasur_root_values(mode, next_values=nxt)
+    r = None
+    for i, t in enumerate(trees):
+        r = t.pasur_response_reach(mode, nxt_of[i], root_reach=r)
+    return r
+
+
 def solve_hybrid(P, ctx, decks, cfg, mlp, first_round: int = 0, last_round: int = 2, eps: float = 1e-3,
-                 max_passes: int = 4, torch=None):
+                 max_passes: int = 4, torch=None, select: str = "reach"):
     """Returns (cut batch, stats).  stats: passes, exact roots per pass, wall seconds, and the
     FGT node-updates of every solve (the cut batch's and the exact sub-batches')."""
     def sync():
@@ -51,7 +70,11 @@ def solve_hybrid(P, ctx, decks, cfg, mlp, first_round: int = 0, last_round: int 
         picks = []
         for d in range(n):
             r = root_reach_after_cut(b, d, first_round, last_round)
-            new = (r > eps) & ~exact[d]
+            hit = r > eps
+            if select == "response":
+                for mode in (1, 2):
+                    hit |= response_reach_after_cut(b, d, first_round, last_round, pred[d], mode) > eps
+            new = hit & ~exact[d]
             picks.append(np.nonzero(new)[0])
         total = int(sum(len(x) for x in picks))
         added.append(total)

@@ -36,7 +36,7 @@ EXPORTS = [
     "pasur_batch_create_cut", "pasur_solved_sizes", "pasur_batch_work", "pasur_cfr_convergence",
     "pasur_root_paths", "pasur_cfr_iterate_roots", "pasur_root_sizes", "pasur_round_reach",
     "pasur_batch_create_roots", "pasur_batch_set_cut_values", "pasur_swept_pairs", "pasur_batch_pairs",
-    "pasur_save_round", "pasur_load_round", "pasur_avg_strategy_async", "pasur_sync",
+    "pasur_save_round", "pasur_load_round", "pasur_avg_strategy_async", "pasur_sync", "pasur_response_reach",
 ]
 
 
@@ -97,6 +97,7 @@ def load() -> C.CDLL:
     L.pasur_load_round.argtypes = [vp, vp, C.c_size_t]
     L.pasur_avg_strategy_async.argtypes = [vp, vp, i64]
     L.pasur_sync.argtypes = [vp]
+    L.pasur_response_reach.argtypes = [vp, C.c_int, vp, vp, vp, vp, i64]
     L.pasur_batch_pairs.argtypes = [vp, i64p]
     L.pasur_root_paths.argtypes = [vp, vp, i64]
     L.pasur_cfr_iterate_roots.argtypes = [vp, C.POINTER(pasur_config), vp, i64, i64]
@@ -586,6 +587,16 @@ class Tree:
         rr = None if root_reach is None else np.ascontiguousarray(root_reach, np.float64)
         sg = None if sigma is None else (sigma if hasattr(sigma, "data_ptr") else np.ascontiguousarray(sigma, np.float32))
         self._c(load().pasur_round_reach(self.h, _ptr(sg), _ptr(rr), _ptr(out), self.n_next_roots()))
+        return out[:self.n_next_roots()]
+
+    def pasur_response_reach(self, mode: int, next_values, root_reach=None, sigma=None) -> np.ndarray:
+        """Probability of every next-round root when one player best-responds (mode 1 Alex, 2 Bob;
+        3 both on sigma) and the other follows sigma (default: own sigma-bar)."""
+        out = np.zeros(max(self.n_next_roots(), 1), np.float64)
+        rr = None if root_reach is None else np.ascontiguousarray(root_reach, np.float64)
+        sg = None if sigma is None else (sigma if hasattr(sigma, "data_ptr") else np.ascontiguousarray(sigma, np.float32))
+        nx = next_values if hasattr(next_values, "data_ptr") else np.ascontiguousarray(next_values, np.float64)
+        self._c(load().pasur_response_reach(self.h, mode, _ptr(sg), _ptr(nx), _ptr(rr), _ptr(out), self.n_next_roots()))
         return out[:self.n_next_roots()]
 
     def pasur_root_sizes(self) -> np.ndarray:

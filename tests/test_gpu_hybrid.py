@@ -3,6 +3,7 @@
 - pasur_round_reach: the probability of every next-round root under the average strategies
   conserves probability (each round's roots pass on exactly their own reach) and equals the same
   product of strategies along every path computed from the oracle's tree structure;
+- pasur_response_reach: the same with one player best-responding, against the oracle's values;
 - pasur_batch_create_roots: a batch started from a subset of a round's roots gives those roots
   the utilities of the batch over all roots, bit for bit (roots are independent);
 - pasur_batch_set_cut_values: a cut batch given the exact next-round utilities reproduces the
@@ -68,6 +69,56 @@ def test_round_reach(P, ctx):
     assert np.allclose(r4, want, rtol=1e-12, atol=1e-15)
     for t in (t3, t4):
         t.free()
+
+
+def test_response_reach(P, ctx):
+    """pasur_response_reach: mode 3 is pasur_round_reach (to rounding); with a best responder the
+    probability is still conserved, and it equals the reach computed on the host from the
+    oracle's node values (its best responses: the first best child) and the GPU's strategies."""
+    deck = P.pasur_deal(9)
+    pools = np.array([sum(1 << int(c) for c in deck[:4])], np.uint64)
+    t3 = ctx.pasur_build_round(deck, 3, pools)
+    t3.unfold_single()
+    _, _, c4, _ = t3.pasur_next_roots()
+    rng = np.random.default_rng(11)
+    nxt = rng.normal(0.0, 4.0, len(c4)).astype(np.float32)
+    t3.pasur_cfr_iterate(P.pasur_config_default(iters=T), nxt)
+    nv = nxt.astype(np.float64)
+    # the leaves' reaches are added into their next-round roots in no fixed order: equal to
+    # rounding
+    assert np.allclose(t3.pasur_response_reach(3, nv), t3.pasur_round_reach(), rtol=1e-12, atol=1e-15)
+    ot = O.Tree(deck, 3, pools)
+    ot.unfold_single()
+    _, _, _, lnk = ot.next_roots()
+    leaf = ot.leaf_utilities_linked(lnk, nv)
+    sb = np.asarray(t3.pasur_avg_strategy(), np.float64)
+    q = ot.sizes()[1]
+    for mode in (1, 2):
+        got = t3.pasur_response_reach(mode, nv)
+        assert abs(got.sum() - 1.0) < 1e-5 and (got >= 0).all()
+        vals = ot.node_values(leaf, mode, sb)
+        reach, base = np.ones(int(q[0])), 0
+        for k in range(8):
+            par = ot.fgt_parents(k + 1)
+            sig = sb[base:base + q[k + 1]]
+            base += int(q[k + 1])
+            responder = (mode == 1) == (k % 2 == 0)
+            if responder:
+                v = vals[k + 1]
+                best = {}
+                for i in range(len(par)):  # one slot per root: children of a parent are consecutive
+                    p = int(par[i])
+                    if p not in best or ((v[i] > v[best[p]]) if k % 2 == 0 else (v[i] < v[best[p]])):
+                        best[p] = i
+                chosen = np.zeros(len(par), bool)
+                chosen[list(best.values())] = True
+                reach = np.where(chosen, reach[par], 0.0)
+            else:
+                reach = reach[par] * sig
+        want = np.bincount(lnk, weights=reach, minlength=len(c4))
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-15), (mode, np.abs(got - want).max())
+        print("response reach mode", mode, "roots reached", int((got > 0).sum()), "of", len(got))
+    t3.free()
 
 
 def test_batch_from_roots_and_cut_values(P, ctx):
