@@ -255,7 +255,7 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
         int best = def;
         for (int i = 0; i < 3; i++) {
             int blocks = 0;
-            PASUR_TRY(cfr_occupancy(ctx, cand[i], one.cls_smem[c], one.cls_end[c] - one.cls_begin[c], &blocks));
+            PASUR_TRY(cfr_occupancy(ctx, cand[i], c, one.cls_smem[c], one.cls_end[c] - one.cls_begin[c], &blocks));
             if (blocks <= 0) continue;
             one.cls_threads[c] = cand[i];
             one.cls_blocks[c] = blocks;
@@ -277,7 +277,7 @@ int autotune(pasur_batch *b, CfrPlan &plan) {
         for (CfrPlan &pl : b->plans) {
             if (pl.cls_end[c] == pl.cls_begin[c]) continue;
             int blocks = 0;
-            PASUR_TRY(cfr_occupancy(ctx, best, pl.cls_smem[c], pl.cls_end[c] - pl.cls_begin[c], &blocks));
+            PASUR_TRY(cfr_occupancy(ctx, best, c, pl.cls_smem[c], pl.cls_end[c] - pl.cls_begin[c], &blocks));
             if (blocks > 0) {
                 pl.cls_threads[c] = best;
                 pl.cls_blocks[c] = blocks;

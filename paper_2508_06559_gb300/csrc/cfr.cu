@@ -472,8 +472,8 @@ __device__ __forceinline__ void run_item(const CfrParams &p, const TreeView &tv,
     __syncthreads();
 }
 
-template <int VARIANT, int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_cfr_items(CfrParams p) {
+template <int VARIANT, int MAXT, int MINB = (MAXT == 256 ? 3 : 1)>
+__global__ void __launch_bounds__(MAXT, MINB) k_cfr_items(CfrParams p) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_item;
     __shared__ int32_t s_as[10];
@@ -666,10 +666,12 @@ __global__ void k_stream_finalize(CfrParams p, StreamPlan sp) {
     }
 }
 
-// The instantiation for blocks of `threads` threads: up to 256 threads at up to 80 registers
-// (three 256-thread blocks per SM), up to 512 at up to 128 (no spills), up to 1024 at 64 (the
-// register file of one SM).
-const void *cfr_kernel_for(int variant, int threads) {
+// The instantiation for blocks of `threads` threads of size class c: up to 256 threads at up to 80
+// registers (three 256-thread blocks per SM), class 3 (two blocks per SM by its shared memory) at
+// up to 128 (96 used: seed-47 CFR 1111 -> 1087 ms against 80), up to 512 at up to 128 (no spills),
+// up to 1024 at 64 (the register file of one SM).
+const void *cfr_kernel_for(int variant, int threads, int cls) {
+    if (threads <= 256 && cls == 3) return variant == 1 ? (const void *)k_cfr_items<1, 256, 2> : (const void *)k_cfr_items<0, 256, 2>;
     if (threads <= 256) return variant == 1 ? (const void *)k_cfr_items<1, 256> : (const void *)k_cfr_items<0, 256>;
     if (threads <= 512) return variant == 1 ? (const void *)k_cfr_items<1, 512> : (const void *)k_cfr_items<0, 512>;
     return variant == 1 ? (const void *)k_cfr_items<1, 1024> : (const void *)k_cfr_items<0, 1024>;
@@ -1927,7 +1929,8 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         PASUR_TRY(cfr_dyn_smem_limit(ctx, &lim));
         for (int v = 0; v < 2; v++)
             for (int t : {256, 512, 1024})
-                PASUR_CUDA(ctx, cudaFuncSetAttribute(cfr_kernel_for(v, t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+                for (int c : {0, 3})
+                    PASUR_CUDA(ctx, cudaFuncSetAttribute(cfr_kernel_for(v, t, c), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
         ctx->cfr_smem_raised = true;
     }
     for (int c = 0; c < kNumCls; c++) {
@@ -1950,16 +1953,16 @@ int cfr_finalize_plan(pasur_ctx *ctx, CfrPlan &plan, std::vector<CfrItem> *cls_i
         plan.cls_threads[c] = threads;
         if (n == 0) continue;
         int per_sm = 0;
-        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads), threads, plan.cls_smem[c]));
+        PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads, c), threads, plan.cls_smem[c]));
         if (per_sm < 1) return set_err(ctx, PASUR_EINVAL, "CFR kernel cannot be resident with this shared-memory plan");
         plan.cls_blocks[c] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n));
     }
     return PASUR_OK;
 }
 
-int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks) {
+int cfr_occupancy(pasur_ctx *ctx, int threads, int cls, size_t smem, int64_t n_items, int *blocks) {
     int per_sm = 0;
-    PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads), threads, smem));
+    PASUR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cfr_kernel_for(0, threads, cls), threads, smem));
     *blocks = per_sm < 1 ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->num_sms, n_items));
     return PASUR_OK;
 }
@@ -2054,7 +2057,7 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
         p.i_end = plan.cls_end[c];
         p.counter = ctx->counter + c;
         void *args[] = {&p};
-        PASUR_CUDA(ctx, cudaLaunchKernel(cfr_kernel_for(cfg->variant, plan.cls_threads[c]), dim3((unsigned)plan.cls_blocks[c]),
+        PASUR_CUDA(ctx, cudaLaunchKernel(cfr_kernel_for(cfg->variant, plan.cls_threads[c], c), dim3((unsigned)plan.cls_blocks[c]),
                                          dim3((unsigned)plan.cls_threads[c]), args, plan.cls_smem[c], st));
         ctx->launches++;
         PASUR_CUDA(ctx, cudaEventRecord(ctx->cls_t1[c], st));

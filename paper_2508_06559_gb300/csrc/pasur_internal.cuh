@@ -439,7 +439,7 @@ int cfr_launch_plan(pasur_ctx *ctx, CfrPlan &plan, const pasur_config *cfg, int6
 void cfr_plan_times(pasur_ctx *ctx, CfrPlan &plan);
 int cfr_dcfr_factors(pasur_ctx *ctx, const pasur_config *cfg, int64_t t0, float **out, size_t *bytes);
 // blocks of a persistent CFR launch with this block size and shared memory (0 if it cannot run)
-int cfr_occupancy(pasur_ctx *ctx, int threads, size_t smem, int64_t n_items, int *blocks);
+int cfr_occupancy(pasur_ctx *ctx, int threads, int cls, size_t smem, int64_t n_items, int *blocks);
 int cfr_export_sigma(const pasur_tree *t, float *out_dev);
 // average strategies of the solved slots only (levels 1..8, solved FGT order, sum of cQ[1..8])
 int export_sigma_solved(const pasur_tree *t, float *out_dev);
