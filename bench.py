@@ -36,15 +36,22 @@ WORKLOADS = {
     "batch64": (3, "64 seeded deals (seeds S..S+63), rounds 4-6 (0-based 3-5) of each from the standalone root, "
                    "solved together: one merged persistent launch per round and size class under a CUDA graph"),
     "surrogate64": (0, "64 seeded deals (seeds S..S+63): rounds 1-3 (0-based 0-2) solved in one batch with the "
-                       "leaves of round 3 valued by the trained surrogate at the round-4 roots, the round-4 roots "
-                       "the play reaches with probability above eps then solved exactly (rounds 4-6 from those "
-                       "roots only) and rounds 1-3 solved again, until no new root; against the exact batched solve "
-                       "of all six rounds"),
+                       "leaves of round 3 valued by the trained surrogate at the round-4 roots; 10 % of every "
+                       "deal's round-4 pools solved exactly (rounds 4-6 from those roots only), a copy of the "
+                       "surrogate tuned on their exact utilities, the other roots valued by the tuned copy, the "
+                       "sampled ones by their exact utilities, and rounds 1-3 solved again; against the exact "
+                       "batched solve of all six rounds"),
 }
 SUR_DEALS = 64
-HYBRID_EPS = 1e-3       # the timed form's reach threshold
-HYBRID_FRONTIER = (None, 1e-2, 1e-3, 1e-4, 0.0)  # None = the surrogate alone
-HYBRID_RESPONSE_FRONTIER = (1e-2, 1e-3, 1e-4)     # roots reached by best responses too
+# the timed form: the surrogate tuned on an exact 10 % sample of the deals' round-4 pools
+HYBRID_TIMED = dict(eps=None, tune_frac=0.1, tune_scope="batch")
+# frontier forms: (eps, select, tune_frac, tune_scope); eps None = no fallback passes, eps and
+# select = the exact fallback for the roots the average strategies ("reach") or best responses
+# too ("response") reach with probability above eps
+HYBRID_FORMS = ([(None, "reach", 0.0, "batch")] + [(e, "reach", 0.0, "batch") for e in (1e-2, 1e-3, 1e-4, 0.0)]
+                + [(e, "response", 0.0, "batch") for e in (1e-2, 1e-3, 1e-4)]
+                + [(None, "reach", 0.1, "batch"), (None, "reach", 0.1, "deal"), (None, "reach", 0.2, "batch"),
+                   (1e-3, "response", 0.1, "batch"), (1e-3, "response", 0.2, "batch")])
 SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..), rounds 4-6 from the standalone root
 SUR_LABEL_ITERS = 300
 BATCH_DEALS = 64
@@ -276,24 +283,26 @@ def surrogate_setup(P, ctx, decks, T, torch):
         return ex
 
     frontier = []
-    forms = [(eps, "reach") for eps in HYBRID_FRONTIER] + [(eps, "response") for eps in HYBRID_RESPONSE_FRONTIER]
-    for eps, select in forms:
+    for eps, select, frac, scope in HYBRID_FORMS:
         for key, net in (("surrogate", mlp), ("no_learning", none)):
-            if key == "no_learning" and (eps is not None or select != "reach"):
+            if key == "no_learning" and (eps is not None or select != "reach" or frac > 0):
                 continue
             torch.cuda.synchronize()
-            if eps is None:
+            if eps is None and frac == 0:
                 t2 = time.perf_counter()
                 bs = P.Batch(ctx, decks, 0, cfg, last_round=2, mlp=net)
                 bs.pasur_batch_solve()
                 torch.cuda.synchronize()
                 st = dict(passes=0, exact_roots=0, wall_s=time.perf_counter() - t2)
             else:
-                bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch, select=select)
+                bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch, select=select,
+                                        tune_frac=frac, tune_scope=scope)
             ex = judge(bs)
             bs.free()
             gap = float(np.mean(ex)) - float(np.mean(expl_exact))
-            frontier.append({"net": key, "eps": eps, "select": select, "create_solve_s": st["wall_s"],
+            frontier.append({"net": key, "eps": eps, "select": select, "tune_frac": frac,
+                             "tune_scope": scope if frac > 0 else None, "create_solve_s": st["wall_s"],
+                             "tune_s": st.get("tune_s", 0.0),
                              "speedup_vs_exact": exact_s / st["wall_s"], "exploitability_mean": float(np.mean(ex)),
                              "gap_vs_exact": gap, "max_deal_gap": float(np.max(np.array(ex) - np.array(expl_exact))),
                              "passes": st["passes"], "exact_round4_roots": st["exact_roots"],
@@ -306,16 +315,16 @@ def surrogate_setup(P, ctx, decks, T, torch):
         "train_loss_first_last": [float(losses[0]), float(losses[-1])],
         "exact_batch_s": exact_s, "exact_node_updates": exact_edges * T,
         "exploitability_mean_exact": float(np.mean(expl_exact)),
-        "frontier": frontier, "timed_eps": HYBRID_EPS, "target_gap": 1e-3})
+        "frontier": frontier, "timed_form": HYBRID_TIMED, "target_gap": 1e-3})
 
 
 def solve_surrogate(P, ctx, decks, first_round: int, T: int, out_device: bool, torch):
     """One step of the surrogate workload: rounds 1-3 of every deal batched with the surrogate at
-    the round-4 roots and the exact fallback for the roots reached with probability above
-    HYBRID_EPS; then every tree's average strategies and root utilities written out."""
+    the round-4 roots, tuned on an exact sample of them (HYBRID_TIMED); then every tree's average
+    strategies and root utilities written out."""
     from paper_2508_06559_gb300 import hybrid as H
     cfg = P.pasur_config_default(iters=T, **SOLVER)
-    b, st = H.solve_hybrid(P, ctx, decks, cfg, _SUR["mlp"], 0, 2, eps=HYBRID_EPS, torch=torch)
+    b, st = H.solve_hybrid(P, ctx, decks, cfg, _SUR["mlp"], 0, 2, torch=torch, **HYBRID_TIMED)
     ms, edges, _ = b.pasur_batch_stats()
     solved, swept = b.pasur_batch_work()
     _WORK.update(solved=solved * T, swept=swept * T, pairs=b.pasur_batch_pairs() * T)
@@ -641,7 +650,9 @@ def run_ours(args, rank, world, dist):
         si["speedup_vs_exact_timed"] = si["exact_batch_s"] / (ms_per_step / 1e3)
         si["note"] = ("exploitability = (BR_Alex - BR_Bob) / 2 of the whole-game profile (rounds 1-3 from the solve "
                       "under test, rounds 4-6 exact), fp64 best-response chain over all six exact rounds; speedups "
-                      "compare whole create+solve wall times of the batched forms; eps None = the surrogate alone")
+                      "compare whole create+solve wall times of the batched forms; eps None = no fallback passes; "
+                      "tune_frac = the share of every deal's round-4 pools solved exactly to tune a copy of the "
+                      "surrogate (tune_scope deal: one copy per deal, batch: one for all deals)")
         line["surrogate"] = si
     return line
 

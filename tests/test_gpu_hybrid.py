@@ -9,7 +9,10 @@
 - pasur_batch_set_cut_values: a cut batch given the exact next-round utilities reproduces the
   exact batch's early rounds bit for bit;
 - the fallback loop runs and, solving every reached root exactly, ends with an exploitability no
-  worse than the surrogate alone.
+  worse than the surrogate alone;
+- tuning a copy of the surrogate on an exact sample of the roots after the cut: with every pool
+  sampled the early rounds are the exact batch's bit for bit; with a partial sample the copy fits
+  its sample better than the network it started from, which stays unchanged.
 """
 import numpy as np
 import pytest
@@ -190,5 +193,73 @@ def test_fallback_loop(P, ctx):
     assert st["exact_roots"] > 0 and st["exact_roots_added"][-1] == 0
     assert e_hyb.mean() <= e_alone.mean() + 1e-9
     b.free()
+    net.free()
+    full.free()
+
+
+@pytest.mark.parametrize("scope", ["batch", "deal"])
+def test_tuned_cut(P, ctx, scope):
+    """Tuning a copy of the surrogate on an exact sample of the round-4 pools: with every pool
+    sampled every root after the cut is exact and the cut batch's rounds 1-3 are the exact batch's
+    bit for bit; with a partial sample the sampled roots are counted as exact, the same seeded
+    sample is drawn again, the tuning loss falls, the tuned copy fits the exact sample better than
+    the network it starts from, and the network itself is left as it was."""
+    import torch
+
+    from paper_2508_06559_gb300 import hybrid as H
+    decks = np.stack([P.pasur_deal(s) for s in SEEDS])
+    cfg = P.pasur_config_default(iters=T, threads=128)
+    full = P.Batch(ctx, decks, 0, cfg)
+    full.pasur_batch_solve()
+    net = P.Mlp(ctx, seed=3)
+    params0 = net.get_params()
+    b, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=None, torch=torch, tune_frac=1.0, tune_scope=scope,
+                           tune_epochs=3)
+    assert st["passes"] == 0 and st["exact_roots"] == st["roots_after_cut"] == st["tune_roots"] > 0
+    for d in range(len(SEEDS)):
+        for r in range(3):
+            x, y = b.pasur_batch_tree(d, r), full.pasur_batch_tree(d, r)
+            assert np.array_equal(x.pasur_round_utilities(), y.pasur_round_utilities())
+            assert np.array_equal(x.pasur_avg_strategy(), y.pasur_avg_strategy())
+    b.free()
+    sampled = []
+    for _ in range(2):
+        b, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=None, torch=torch, tune_frac=0.3, tune_scope=scope,
+                               tune_epochs=20, tune_seed=4)
+        assert 0 < st["tune_roots"] == st["exact_roots"] < st["roots_after_cut"]
+        assert len(st["tune_loss_first_last"]) == (len(SEEDS) if scope == "deal" else 1)
+        for first, last in st["tune_loss_first_last"]:
+            assert np.isfinite(first) and last < first
+        sampled.append(st["tune_roots"])
+        b.free()
+    assert sampled[0] == sampled[1]  # the sample is seeded
+    # the tuned copy fits its exact sample better than the network it starts from.  Two tunings
+    # are not bit-identical: training sums the weight gradients with atomics (split K), and Adam's
+    # first steps move every weight by about lr whatever its gradient's size, so a gradient near
+    # zero whose sign the summation order flips moves that weight the other way
+    cut = full.pasur_batch_tree(0, 2)
+    pools, soff, scores, _ = cut.pasur_next_roots()
+    sel = H.sample_pools(np.asarray(pools), np.asarray(soff), 0.3, np.random.default_rng(0))
+    roots = [H.roots_subset(np.asarray(pools), np.asarray(soff), np.asarray(scores), sel)]
+    e = P.Batch(ctx, decks[:1], 3, cfg, roots=roots)
+    e.pasur_batch_solve()
+    et = e.pasur_batch_tree(0, 3)
+    u = np.asarray(et.pasur_round_utilities(), np.float64)
+    base = np.asarray(net.predict_next(cut), np.float64)[sel]
+    tuner = P.Mlp(ctx, dataset_capacity=len(sel))
+    preds = []
+    for _ in range(2):
+        losses = H.tune_copy(net, tuner, [et], 30, 1e-3, seed=2)
+        assert len(losses) == 30 and losses[-1] < losses[0]
+        preds.append(np.asarray(tuner.predict_next(cut), np.float64))
+    fits = [float(np.mean((p[sel] - u) ** 2)) for p in preds]
+    assert max(fits) < np.mean((base - u) ** 2)
+    assert abs(fits[0] - fits[1]) <= 0.1 * max(fits)
+    assert np.max(np.abs(preds[0] - preds[1])) <= 0.1
+    assert np.array_equal(net.get_params(), params0)
+    tuner.free()
+    e.free()
+    with pytest.raises(ValueError):
+        H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=None, tune_frac=0.3, tune_scope="everything")
     net.free()
     full.free()
