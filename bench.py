@@ -52,7 +52,8 @@ HYBRID_FORMS = ([(None, "reach", 0.0, "batch")] + [(e, "reach", 0.0, "batch") fo
                 + [(e, "response", 0.0, "batch") for e in (1e-2, 1e-3, 1e-4)]
                 + [(None, "reach", 0.1, "batch"), (None, "reach", 0.1, "deal"), (None, "reach", 0.2, "batch"),
                    (1e-3, "response", 0.1, "batch"), (1e-3, "response", 0.2, "batch")])
-SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..), rounds 4-6 from the standalone root
+SUR_TRAIN_DEALS = 4096   # training deals (seeds 10000..)
+SUR_TRAIN_FRAC = 0.1     # share of each training deal's round-4 pools solved for labels
 SUR_LABEL_ITERS = 300
 BATCH_DEALS = 64
 METRIC = "CFR node-updates/sec"
@@ -249,20 +250,30 @@ def surrogate_setup(P, ctx, decks, T, torch):
     best-response chain over the six exact rounds)."""
     from paper_2508_06559_gb300 import hybrid as H
     t0 = time.perf_counter()
+    none = P.Mlp(ctx)
+    none.set_params(no_learning_params(P))
     mlp = P.Mlp(ctx, dataset_capacity=2_000_000, seed=7)
     cfg_l = P.pasur_config_default(iters=SUR_LABEL_ITERS)
+    # labels on the roots the surrogate is asked about: round-4 roots that play reaches from the
+    # deal's start (rounds 1-3 built, not solved), a seeded sample of each deal's pools solved exactly
     for i in range(0, SUR_TRAIN_DEALS, 64):
-        b = P.Batch(ctx, np.stack([P.pasur_deal(10000 + i + j) for j in range(64)]), 3, cfg_l)
+        dk = np.stack([P.pasur_deal(10000 + i + j) for j in range(64)])
+        cut = P.Batch(ctx, dk, 0, cfg_l, last_round=2, mlp=none)
+        roots = []
+        for d in range(64):
+            pools, soff, scores, _ = cut.pasur_batch_tree(d, 2).pasur_next_roots()
+            pools, soff, scores = np.asarray(pools, np.uint64), np.asarray(soff, np.int64), np.asarray(scores, np.int16)
+            sel = H.sample_pools(pools, soff, SUR_TRAIN_FRAC, np.random.default_rng([1, i + d]))
+            roots.append(H.roots_subset(pools, soff, scores, sel))
+        cut.free()
+        b = P.Batch(ctx, dk, 3, cfg_l, roots=roots)
         b.pasur_batch_solve()
         for d in range(64):
-            for r in (3, 4, 5):
-                mlp.dataset_add_tree(b.pasur_batch_tree(d, r))
+            mlp.dataset_add_tree(b.pasur_batch_tree(d, 3))
         b.free()
     gen_s = time.perf_counter() - t0
     losses = mlp.train(5, 1024, 1e-3, shuffle_seed=1)
     train_ms, steps = mlp.stats()
-    none = P.Mlp(ctx)
-    none.set_params(no_learning_params(P))
     cfg = P.pasur_config_default(iters=T, **SOLVER)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -310,7 +321,8 @@ def surrogate_setup(P, ctx, decks, T, torch):
     be.free()
     none.free()
     _SUR.update(mlp=mlp, info={
-        "deals": len(decks), "train_deals": SUR_TRAIN_DEALS, "train_rows": mlp.dataset_size(),
+        "deals": len(decks), "train_deals": SUR_TRAIN_DEALS, "train_pool_frac": SUR_TRAIN_FRAC,
+        "train_rows": mlp.dataset_size(),
         "label_iters": SUR_LABEL_ITERS, "data_gen_s": gen_s, "train_ms": train_ms, "adam_steps": steps,
         "train_loss_first_last": [float(losses[0]), float(losses[-1])],
         "exact_batch_s": exact_s, "exact_node_updates": exact_edges * T,
