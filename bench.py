@@ -244,8 +244,8 @@ def no_learning_params(P):
 
 def surrogate_setup(P, ctx, decks, T, torch):
     """Untimed: train the surrogate on exact solves of other deals, solve the bench deals exactly
-    (batched, all six rounds, timed for the speedups), then the surrogate's cut at every eps of the
-    frontier (create + solve + exact-fallback passes, timed), each judged by the exploitability of
+    (batched, all six rounds, timed for the speedups), then the surrogate's cut in every form of the
+    frontier (create + solve + tuning and exact passes, timed), each measured by the exploitability of
     its whole-game profile (rounds 1-3 from the solve under test, rounds 4-6 exact; fp64
     best-response chain over the six exact rounds)."""
     from paper_2508_06559_gb300 import hybrid as H
@@ -286,7 +286,7 @@ def surrogate_setup(P, ctx, decks, T, torch):
     br = [(P.chain_values(te[d], 1)[0], P.chain_values(te[d], 2)[0]) for d in range(len(decks))]
     expl_exact = [(a - b) / 2 for a, b in br]
 
-    def judge(bs):
+    def exploitability_of(bs):
         ex = []
         for d in range(len(decks)):
             sig = [bs.pasur_batch_tree(d, r).pasur_avg_strategy() for r in range(3)] + [None] * 3
@@ -308,7 +308,7 @@ def surrogate_setup(P, ctx, decks, T, torch):
             else:
                 bs, st = H.solve_hybrid(P, ctx, decks, cfg, net, 0, 2, eps=eps, torch=torch, select=select,
                                         tune_frac=frac, tune_scope=scope)
-            ex = judge(bs)
+            ex = exploitability_of(bs)
             bs.free()
             gap = float(np.mean(ex)) - float(np.mean(expl_exact))
             frontier.append({"net": key, "eps": eps, "select": select, "tune_frac": frac,
